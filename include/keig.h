@@ -1,0 +1,249 @@
+/*
+ * keig.h — C-ABI of the GB300 tensor-train k-eigenvalue library.
+ *
+ * Method: arXiv 2309.03347 ("Tensor networks for solving realistic
+ * time-independent Boltzmann neutron transport equation").  The discretised
+ * k-eigenvalue problem H Psi = (S + F/k) Psi (Eq. (OpFormkNTE)) is solved in a
+ * mixed TT/QTT format (Sec. 3.2-3.4): every operator is a sum of tensor
+ * products of one-dimensional factors (Sec. 3.2.1-3.2.2), turned into QTT by
+ * Algorithm 1, and the fixed point of Eq. (TT_k_eff_fixed_points) runs on TT
+ * vectors with TT linear algebra (Sec. 3.5).
+ *
+ * Conventions for every entry point:
+ *  - Return value: TT_OK (0) or a negative status below.  The message of the
+ *    last failure of a context is returned by tt_last_error() (string owned by
+ *    the context, valid until its next call).
+ *  - All device work is enqueued on the context's CUDA stream; calls that
+ *    return host data (sizes, scalars, copies to host) synchronise it.
+ *  - Handles (tt_ctx, tt_vec, tt_op) are opaque, owned by the caller from
+ *    creation to the matching *_destroy call.  Input arrays are copied; the
+ *    library never keeps a caller pointer after a call returns.
+ *  - Floating point is FP64 unless a tt_prec argument says otherwise.
+ *  - No CPU fallback: without a usable CUDA device every call that needs one
+ *    fails with TT_ECUDA.
+ *
+ * Layouts (all row-major, the first index slowest):
+ *  - TT vector core k: (r_{k-1}, n_k, r_k), r_0 = r_d = 1 (Eq. (TT_def_element)).
+ *    Cores are exchanged as one array, core 0 first.
+ *  - TT matrix core k: (R_{k-1}, m_k, n_k, R_k), output index m (i_k), input
+ *    index n (j_k) (Eq. (TT-matrix-componentwise)).
+ *  - Angular flux Psi: (G, L, n, n, n), x fastest (Appendix A.3, Eq. (aflux)).
+ *    Its TT form has cores [g:G][octant:8][direction:L/8][z bits][y bits]
+ *    [x bits], bits most-significant first, so row-major flattening of the
+ *    dense TT equals that layout.
+ */
+#ifndef KEIG_H
+#define KEIG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  TT_OK = 0,
+  TT_EINVAL = -1,     /* bad argument (sizes, pointers, non-finite input) */
+  TT_ENOMEM = -2,     /* device allocation failed */
+  TT_ECUDA = -3,      /* CUDA runtime error (message holds the CUDA string) */
+  TT_ENOCONV = -4,    /* iteration limit reached; best iterate returned */
+  TT_ETIMEOUT = -5,   /* a bounded device wait gave up */
+  TT_ENONFINITE = -6  /* a NaN/Inf appeared during the computation */
+};
+
+typedef struct tt_ctx tt_ctx;
+typedef struct tt_vec tt_vec;
+typedef struct tt_op tt_op;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context bound to the current CUDA device and to `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  out: new handle. */
+int tt_ctx_create(tt_ctx **out, void *cuda_stream);
+int tt_ctx_destroy(tt_ctx *ctx);
+const char *tt_last_error(const tt_ctx *ctx);
+/* Library version string (static storage). */
+const char *tt_version(void);
+/* Counters since creation or the last reset: kernel launches issued by the
+ * library and algorithmic FP64 flops of the core contractions (the
+ * operator-core x vector-core products: exact matvec, local-system matvecs
+ * and interface updates). */
+int tt_ctx_counters(tt_ctx *ctx, int64_t *launches, double *contraction_flops);
+int tt_ctx_reset_counters(tt_ctx *ctx);
+
+/* ---------------------------------------------------------------- TT vectors */
+
+/* New TT vector with d cores of modes n[0..d-1] and bond ranks r[0..d]
+ * (r[0] = r[d] = 1).  cores == NULL gives zeros; else `cores` holds all core
+ * entries back to back (sum_k r_k n_k r_{k+1} doubles), on the device if
+ * cores_on_device != 0, else on the host. */
+int tt_vec_create(tt_ctx *ctx, int d, const int *n, const int *r, const double *cores,
+                  int cores_on_device, tt_vec **out);
+int tt_vec_destroy(tt_vec *x);
+/* d of x; with n (d ints) and r (d+1 ints) non-NULL also the modes and ranks. */
+int tt_vec_shape(const tt_vec *x, int *d, int *n, int *r);
+/* Number of stored doubles (sum over cores). */
+int tt_vec_numel(const tt_vec *x, size_t *count);
+/* Copy all cores to `dst` (numel doubles), device or host memory. */
+int tt_vec_get_cores(tt_ctx *ctx, const tt_vec *x, double *dst, int dst_on_device);
+/* Dense tensor (prod n_k doubles, row-major) into device memory `dst`
+ * (a test helper for small tensors; TT_EINVAL above 2^28 entries). */
+int tt_vec_to_dense(tt_ctx *ctx, const tt_vec *x, double *dst_device, size_t len);
+/* y = alpha x + beta y in TT form (block concatenation, ranks add), no
+ * rounding: Sec. 2.2 ("the sum of tensors in TT format is itself a tensor in
+ * TT format").  Result replaces *y's cores. */
+int tt_vec_axpby(tt_ctx *ctx, double alpha, const tt_vec *x, double beta, tt_vec *y);
+/* x *= alpha (scales the first core). */
+int tt_vec_scale(tt_ctx *ctx, tt_vec *x, double alpha);
+/* <x, y> and ||x||_F by core-wise contraction (Appendix B.3, the
+ * contraction of a tensor with a vector, applied core by core). */
+int tt_vec_dot(tt_ctx *ctx, const tt_vec *x, const tt_vec *y, double *out);
+int tt_vec_norm(tt_ctx *ctx, const tt_vec *x, double *out);
+/* Sum of all entries (contraction of every core with a vector of ones). */
+int tt_vec_sum(tt_ctx *ctx, const tt_vec *x, double *out);
+
+/* TT rounding in place: left-to-right Householder QR sweep, then a
+ * right-to-left truncated-SVD sweep keeping per bond the fewest singular
+ * values whose discarded tail has norm <= eps ||x||_F / sqrt(d-1), and at
+ * most rmax (rmax <= 0: no cap).  Rounding after TT sums is what Sec. 2.2
+ * and Sec. 3.3 call for ("a rank reduction step could be necessary").
+ * Limits: every bond rank before truncation must be <= 512. */
+int tt_round(tt_ctx *ctx, tt_vec *x, double eps, int rmax);
+
+/* ---------------------------------------------------------------- TT matrices */
+
+int tt_op_create(tt_ctx *ctx, int d, const int *m, const int *n, const int *R, const double *cores,
+                 int cores_on_device, tt_op **out);
+int tt_op_destroy(tt_op *A);
+int tt_op_shape(const tt_op *A, int *d, int *m, int *n, int *R);
+int tt_op_numel(const tt_op *A, size_t *count);
+int tt_op_get_cores(tt_ctx *ctx, const tt_op *A, double *dst, int dst_on_device);
+/* C = alpha A + beta B (new operator, ranks add), then rounded with
+ * (eps, rmax) when eps >= 0.  out: new handle. */
+int tt_op_axpby(tt_ctx *ctx, double alpha, const tt_op *A, double beta, const tt_op *B, double eps,
+                int rmax, tt_op **out);
+
+/* ---------------------------------------------------------------- the problem */
+
+/* The k-eigenvalue problem of Sec. 2.1 as the paper states it: a cube of
+ * n = 2^l vertices per axis with cell-constant multigroup cross sections,
+ * discrete ordinates ordered octant-major (Appendix A.2, Eq. (hat-mu)),
+ * vacuum faces (Eq. (BCS)).  Host arrays, copied by the library. */
+typedef struct {
+  int l;                    /* 2^l grid points per axis, 1 <= l <= 10 */
+  double side[3];           /* domain lengths x, y, z; Delta = side/(2^l - 1) */
+  int G;                    /* energy groups */
+  int n_mat;                /* materials, 1..255 */
+  const double *sig_t;      /* [n_mat][G] total cross section */
+  const double *sig_s;      /* [n_mat][G_to][G_from] scattering g_from -> g_to */
+  const double *nu_sig_f;   /* [n_mat][G] nu * fission cross section */
+  const double *chi;        /* [n_mat][G] fission spectrum */
+  const double *inv_v;      /* [G] 1/v (alpha problem; unused, may be NULL) */
+  const uint8_t *mat;       /* [(2^l-1)^3] cell materials, z-major, x fastest */
+  int n_dir;                /* directions per octant (L/8) */
+  const double *amu, *aeta, *axi; /* [n_dir] absolute direction cosines */
+  const double *w;          /* [n_dir] weights of one octant, 8*sum(w) = 1 */
+  int bc[6];                /* x-,x+,y-,y+,z-,z+; only 0 (vacuum) is accepted */
+} tt_problem;
+
+typedef enum {
+  TT_OP_H = 0, /* streaming + collision, Sec. 3.2.1 */
+  TT_OP_S = 1, /* scattering, Sec. 3.2.2 */
+  TT_OP_F = 2  /* fission, Sec. 3.2.2 */
+} tt_op_kind;
+
+typedef enum {
+  TT_FP64 = 0,        /* every contraction in FP64 */
+  TT_TF32_SPLIT = 1,  /* reserved: contractions on tensor cores (not built) */
+  TT_BF16_SPLIT = 2   /* reserved: contractions on tensor cores (not built) */
+} tt_prec;
+
+/* Build H, S or F as a TT matrix with cores over the modes
+ * [G][8][L/8][2 x 3l]: each rank-1 term of Sec. 3.2 (per octant: the x, y, z
+ * streaming terms and one collision term per material, or one S/F term per
+ * material) is a tensor product of the 1-D factors D+/-, Ip+/-, Ip+/-_noBC,
+ * diagonal angular matrices, octant selectors and group matrices; each
+ * spatial factor is converted to QTT by Algorithm 1 (reshape, index-pair
+ * permutation, TT-SVD) on the device, the heterogeneous material masks are
+ * QTT-compressed the same way, and the terms are summed and rounded with
+ * eps_op (Sec. 3.3, "the QTT format of the operator is the sum over all
+ * boundary conditions").  out: new handle. */
+int tt_build_operator(tt_ctx *ctx, const tt_problem *prob, tt_op_kind kind, double eps_op, tt_op **out);
+
+/* ---------------------------------------------------------------- products and solves */
+
+enum { TT_MV_EXACT = 0, TT_MV_AMEN = 1 };
+
+/* y = scale * A x.  method TT_MV_EXACT: core-wise Kronecker products
+ * (ranks multiply, Sec. 3.5: the "explicit and exact algorithm") followed by
+ * tt_round(eps, rmax) when eps >= 0.  TT_MV_AMEN: the optimisation form of
+ * Eq. (mv_obj) solved core by core with residual enrichment, to relative
+ * accuracy eps and ranks <= rmax, at most max_sweeps sweeps (the paper's
+ * choice, "amen_mv").  *y: new handle. */
+int tt_matvec(tt_ctx *ctx, const tt_op *A, const tt_vec *x, double scale, int method, double eps,
+              int rmax, int max_sweeps, tt_prec prec, tt_vec **y);
+
+/* Solve A x = b by alternating local solves over the cores with residual
+ * enrichment (Sec. 3.5, Eq. (linear_system_obj) and the AMEn method it
+ * names): the local systems are Galerkin projections onto the current
+ * interfaces, solved by restarted GMRES to eps/sqrt(d); the local solution is
+ * split by a truncated SVD (threshold eps/sqrt(d), cap rmax) and enriched
+ * with a rank-`kick` residual direction.  x: initial guess on entry, solution
+ * on return.  sweeps_done / rel_change (may be NULL): sweeps run and the
+ * largest relative change of a local solution in the last sweep.
+ * TT_ENOCONV when max_sweeps ran out (x still holds the last iterate). */
+int tt_solve_local(tt_ctx *ctx, const tt_op *A, const tt_vec *b, tt_vec *x, double eps, int rmax,
+                   int max_sweeps, int kick, tt_prec prec, int *sweeps_done, double *rel_change);
+
+/* ---------------------------------------------------------------- the eigen loop */
+
+typedef struct {
+  double eps;        /* TT truncation tolerance of products and solves */
+  int rmax;          /* TT rank cap of the flux */
+  double tol_k;      /* stop when |k' - k| / k < tol_k ... */
+  double tol_psi;    /* ... and the relative change of Psi is < tol_psi */
+  int max_iter;      /* outer iterations */
+  int solve_sweeps;  /* AMEn sweeps per linear solve */
+  int mv_sweeps;     /* AMEn sweeps per product */
+  int kick;          /* enrichment rank */
+  int scheme;        /* 0: paper, H Psi' = (S + F/k) Psi; 1: (H - S) Psi' = F Psi / k */
+  tt_prec prec;
+  double eps_op;     /* operator rounding tolerance */
+  const double *psi0_cores; /* optional host TT initial guess (rank-1 cores), NULL = ones */
+} keig_opts;
+
+typedef struct {
+  double k;          /* final eigenvalue */
+  int iters;         /* outer iterations run */
+  double dk_last;    /* |k' - k| / k of the last iteration */
+  double wall_ms;    /* time from entry to return */
+  int max_rank;      /* largest bond rank of the final Psi */
+  double k_hist[512];/* k after each outer iteration (first 512) */
+  double t_hist[512];/* ms since entry at the end of each outer iteration */
+} keig_result;
+
+/* Fill opts with defaults (eps 1e-7, rmax 64, tol_k 1e-9, tol_psi 1e-5,
+ * max_iter 400, solve_sweeps 2, mv_sweeps 2, kick 4, scheme 0, FP64,
+ * eps_op 1e-12). */
+int keig_default_opts(keig_opts *opts);
+
+/* The QTT fixed point of Eq. (TT_k_eff_fixed_points):
+ *   B = (S + F/k) Psi;  H Psi' = B;  k' = k sum(F Psi') / sum(F Psi),
+ * with Psi normalised each iteration so that sum(F Psi) = 1.  The sum of all
+ * entries of F Psi is the dot product of Psi with the TT vector F^T 1, built
+ * once.  Builds H, S, F from `prob` (included in wall_ms).
+ * psi_out (may be NULL): new handle with the final flux.
+ * phi_out (may be NULL): host buffer of G*n^3 doubles receiving the scalar
+ * flux phi[g][k][j][i] = sum_l w_l psi (dense; small grids only). */
+int keig_fixed_point(tt_ctx *ctx, const tt_problem *prob, const keig_opts *opts, keig_result *out,
+                     tt_vec **psi_out, double *phi_out);
+
+/* Scalar flux of a flux TT (contract the octant and direction cores with the
+ * quadrature weights, Appendix B.4) as a TT with cores [G][2 x 3l]. */
+int tt_scalar_flux(tt_ctx *ctx, const tt_vec *psi, const double *w_host, int n_dir, tt_vec **phi);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KEIG_H */

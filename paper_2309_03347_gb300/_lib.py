@@ -1,0 +1,411 @@
+"""ctypes marshalling for libkeig_tt.so.  Names follow include/keig.h."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+TT_OK, TT_EINVAL, TT_ENOMEM, TT_ECUDA, TT_ENOCONV, TT_ETIMEOUT, TT_ENONFINITE = 0, -1, -2, -3, -4, -5, -6
+TT_OP_H, TT_OP_S, TT_OP_F = 0, 1, 2
+TT_MV_EXACT, TT_MV_AMEN = 0, 1
+TT_FP64 = 0
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_FILE = os.path.join(_HERE, "_build", "libkeig_tt.so")
+_lock = threading.Lock()
+_lib = None
+
+D = C.POINTER(C.c_double)
+I = C.POINTER(C.c_int)
+
+
+class KeigError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class TTProblem(C.Structure):
+    _fields_ = [
+        ("l", C.c_int), ("side", C.c_double * 3), ("G", C.c_int), ("n_mat", C.c_int),
+        ("sig_t", D), ("sig_s", D), ("nu_sig_f", D), ("chi", D), ("inv_v", D),
+        ("mat", C.POINTER(C.c_uint8)), ("n_dir", C.c_int),
+        ("amu", D), ("aeta", D), ("axi", D), ("w", D), ("bc", C.c_int * 6),
+    ]
+
+
+class KeigOpts(C.Structure):
+    _fields_ = [
+        ("eps", C.c_double), ("rmax", C.c_int), ("tol_k", C.c_double), ("tol_psi", C.c_double),
+        ("max_iter", C.c_int), ("solve_sweeps", C.c_int), ("mv_sweeps", C.c_int), ("kick", C.c_int),
+        ("scheme", C.c_int), ("prec", C.c_int), ("eps_op", C.c_double), ("psi0_cores", D),
+    ]
+
+
+class KeigResult(C.Structure):
+    _fields_ = [
+        ("k", C.c_double), ("iters", C.c_int), ("dk_last", C.c_double), ("wall_ms", C.c_double),
+        ("max_rank", C.c_int), ("k_hist", C.c_double * 512), ("t_hist", C.c_double * 512),
+    ]
+
+
+def lib_path() -> str:
+    return _LIB_FILE
+
+
+def load():
+    """Load libkeig_tt.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_LIB_FILE):
+            raise ImportError(f"libkeig_tt.so not built ({_LIB_FILE}); run __graft_entry__.build()")
+        lib = C.CDLL(_LIB_FILE)
+        P = C.c_void_p
+        sig = {
+            "tt_ctx_create": ([C.POINTER(P), P], C.c_int),
+            "tt_ctx_destroy": ([P], C.c_int),
+            "tt_last_error": ([P], C.c_char_p),
+            "tt_version": ([], C.c_char_p),
+            "tt_ctx_counters": ([P, C.POINTER(C.c_int64), D], C.c_int),
+            "tt_ctx_reset_counters": ([P], C.c_int),
+            "tt_vec_create": ([P, C.c_int, I, I, D, C.c_int, C.POINTER(P)], C.c_int),
+            "tt_vec_destroy": ([P], C.c_int),
+            "tt_vec_shape": ([P, I, I, I], C.c_int),
+            "tt_vec_numel": ([P, C.POINTER(C.c_size_t)], C.c_int),
+            "tt_vec_get_cores": ([P, P, D, C.c_int], C.c_int),
+            "tt_vec_to_dense": ([P, P, D, C.c_size_t], C.c_int),
+            "tt_vec_axpby": ([P, C.c_double, P, C.c_double, P], C.c_int),
+            "tt_vec_scale": ([P, P, C.c_double], C.c_int),
+            "tt_vec_dot": ([P, P, P, D], C.c_int),
+            "tt_vec_norm": ([P, P, D], C.c_int),
+            "tt_vec_sum": ([P, P, D], C.c_int),
+            "tt_round": ([P, P, C.c_double, C.c_int], C.c_int),
+            "tt_op_create": ([P, C.c_int, I, I, I, D, C.c_int, C.POINTER(P)], C.c_int),
+            "tt_op_destroy": ([P], C.c_int),
+            "tt_op_shape": ([P, I, I, I, I], C.c_int),
+            "tt_op_numel": ([P, C.POINTER(C.c_size_t)], C.c_int),
+            "tt_op_get_cores": ([P, P, D, C.c_int], C.c_int),
+            "tt_op_axpby": ([P, C.c_double, P, C.c_double, P, C.c_double, C.c_int, C.POINTER(P)], C.c_int),
+            "tt_build_operator": ([P, C.POINTER(TTProblem), C.c_int, C.c_double, C.POINTER(P)], C.c_int),
+            "tt_matvec": ([P, P, P, C.c_double, C.c_int, C.c_double, C.c_int, C.c_int, C.c_int, C.POINTER(P)],
+                          C.c_int),
+            "tt_solve_local": ([P, P, P, P, C.c_double, C.c_int, C.c_int, C.c_int, C.c_int, I, D], C.c_int),
+            "keig_default_opts": ([C.POINTER(KeigOpts)], C.c_int),
+            "keig_fixed_point": ([P, C.POINTER(TTProblem), C.POINTER(KeigOpts), C.POINTER(KeigResult),
+                                  C.POINTER(P), D], C.c_int),
+            "tt_scalar_flux": ([P, P, D, C.c_int, C.POINTER(P)], C.c_int),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = lib
+        return lib
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(D)
+
+
+def _ip(a):
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    return a, a.ctypes.data_as(I)
+
+
+class Context:
+    """A tt_ctx bound to the current CUDA device and a torch CUDA stream."""
+
+    def __init__(self, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise KeigError(TT_ECUDA, "CUDA device required (no CPU fallback)")
+        self.lib = load()
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = C.c_void_p()
+        self._check(self.lib.tt_ctx_create(C.byref(h), C.c_void_p(stream.cuda_stream)), None)
+        self.h = h
+
+    def _check(self, rc, h="self"):
+        if rc != TT_OK:
+            hh = self.h if h == "self" else None
+            msg = self.lib.tt_last_error(hh).decode() if hh else "tt_ctx_create failed"
+            raise KeigError(rc, msg)
+
+    def check(self, rc):
+        self._check(rc)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.tt_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def counters(self):
+        n = C.c_int64()
+        f = C.c_double()
+        self.check(self.lib.tt_ctx_counters(self.h, C.byref(n), C.byref(f)))
+        return int(n.value), float(f.value)
+
+    def reset_counters(self):
+        self.check(self.lib.tt_ctx_reset_counters(self.h))
+
+
+class TTVec:
+    """Owning wrapper of a tt_vec handle."""
+
+    def __init__(self, ctx: Context, handle):
+        self.ctx = ctx
+        self.h = handle
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            self.ctx.lib.tt_vec_destroy(self.h)
+            self.h = None
+
+    @property
+    def shape(self):
+        d = C.c_int()
+        self.ctx.check(self.ctx.lib.tt_vec_shape(self.h, C.byref(d), None, None))
+        n = np.zeros(d.value, np.int32)
+        r = np.zeros(d.value + 1, np.int32)
+        self.ctx.check(self.ctx.lib.tt_vec_shape(self.h, C.byref(d), n.ctypes.data_as(I), r.ctypes.data_as(I)))
+        return list(n), list(r)
+
+    @property
+    def ranks(self):
+        return self.shape[1]
+
+    def cores(self) -> List[np.ndarray]:
+        n, r = self.shape
+        cnt = C.c_size_t()
+        self.ctx.check(self.ctx.lib.tt_vec_numel(self.h, C.byref(cnt)))
+        buf = np.empty(cnt.value)
+        self.ctx.check(self.ctx.lib.tt_vec_get_cores(self.ctx.h, self.h, _dp(buf), 0))
+        out, off = [], 0
+        for k in range(len(n)):
+            sz = r[k] * n[k] * r[k + 1]
+            out.append(buf[off:off + sz].reshape(r[k], n[k], r[k + 1]).copy())
+            off += sz
+        return out
+
+    def dense_cuda(self):
+        import torch
+        n, _ = self.shape
+        t = torch.empty(int(np.prod(n)), dtype=torch.float64, device="cuda")
+        self.ctx.check(self.ctx.lib.tt_vec_to_dense(self.ctx.h, self.h, C.cast(t.data_ptr(), D), t.numel()))
+        return t.reshape([int(v) for v in n])
+
+    def dot(self, other: "TTVec") -> float:
+        v = C.c_double()
+        self.ctx.check(self.ctx.lib.tt_vec_dot(self.ctx.h, self.h, other.h, C.byref(v)))
+        return v.value
+
+    def norm(self) -> float:
+        v = C.c_double()
+        self.ctx.check(self.ctx.lib.tt_vec_norm(self.ctx.h, self.h, C.byref(v)))
+        return v.value
+
+    def sum(self) -> float:
+        v = C.c_double()
+        self.ctx.check(self.ctx.lib.tt_vec_sum(self.ctx.h, self.h, C.byref(v)))
+        return v.value
+
+    def scale(self, a: float):
+        self.ctx.check(self.ctx.lib.tt_vec_scale(self.ctx.h, self.h, float(a)))
+
+    def axpby(self, a: float, x: "TTVec", b: float):
+        """self = a x + b self (ranks add)."""
+        self.ctx.check(self.ctx.lib.tt_vec_axpby(self.ctx.h, float(a), x.h, float(b), self.h))
+
+
+class TTOp:
+    def __init__(self, ctx: Context, handle):
+        self.ctx = ctx
+        self.h = handle
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            self.ctx.lib.tt_op_destroy(self.h)
+            self.h = None
+
+    @property
+    def shape(self):
+        d = C.c_int()
+        self.ctx.check(self.ctx.lib.tt_op_shape(self.h, C.byref(d), None, None, None))
+        m = np.zeros(d.value, np.int32)
+        n = np.zeros(d.value, np.int32)
+        R = np.zeros(d.value + 1, np.int32)
+        self.ctx.check(self.ctx.lib.tt_op_shape(self.h, C.byref(d), m.ctypes.data_as(I), n.ctypes.data_as(I),
+                                                R.ctypes.data_as(I)))
+        return list(m), list(n), list(R)
+
+    def cores(self) -> List[np.ndarray]:
+        m, n, R = self.shape
+        cnt = C.c_size_t()
+        self.ctx.check(self.ctx.lib.tt_op_numel(self.h, C.byref(cnt)))
+        buf = np.empty(cnt.value)
+        self.ctx.check(self.ctx.lib.tt_op_get_cores(self.ctx.h, self.h, _dp(buf), 0))
+        out, off = [], 0
+        for k in range(len(m)):
+            sz = R[k] * m[k] * n[k] * R[k + 1]
+            out.append(buf[off:off + sz].reshape(R[k], m[k], n[k], R[k + 1]).copy())
+            off += sz
+        return out
+
+
+# ---------------------------------------------------------------- C-ABI names
+
+def tt_ctx_create(stream=None) -> Context:
+    return Context(stream)
+
+
+def _cat(cores: Sequence):
+    """Concatenate cores given as numpy arrays (host) or torch CUDA tensors (device)."""
+    first = cores[0]
+    if hasattr(first, "is_cuda") and first.is_cuda:
+        import torch
+        flat = torch.cat([c.reshape(-1).to(torch.float64) for c in cores]).contiguous()
+        return flat, C.cast(flat.data_ptr(), D), 1
+    flat = np.ascontiguousarray(np.concatenate([np.asarray(c, dtype=np.float64).ravel() for c in cores]))
+    return flat, _dp(flat), 0
+
+
+def tt_vec_create(ctx: Context, cores: Sequence) -> TTVec:
+    n = [int(c.shape[1]) for c in cores]
+    r = [1] + [int(c.shape[2]) for c in cores]
+    na, npp = _ip(n)
+    ra, rp = _ip(r)
+    flat, ptr, dev = _cat(cores)
+    h = C.c_void_p()
+    ctx.check(ctx.lib.tt_vec_create(ctx.h, len(n), npp, rp, ptr, dev, C.byref(h)))
+    return TTVec(ctx, h)
+
+
+def tt_op_create(ctx: Context, cores: Sequence) -> TTOp:
+    m = [int(c.shape[1]) for c in cores]
+    n = [int(c.shape[2]) for c in cores]
+    R = [1] + [int(c.shape[3]) for c in cores]
+    ma, mp = _ip(m)
+    na, npp = _ip(n)
+    Ra, Rp = _ip(R)
+    flat, ptr, dev = _cat(cores)
+    h = C.c_void_p()
+    ctx.check(ctx.lib.tt_op_create(ctx.h, len(m), mp, npp, Rp, ptr, dev, C.byref(h)))
+    return TTOp(ctx, h)
+
+
+def tt_round(ctx: Context, x: TTVec, eps: float, rmax: int = 0) -> TTVec:
+    ctx.check(ctx.lib.tt_round(ctx.h, x.h, float(eps), int(rmax)))
+    return x
+
+
+def tt_op_axpby(ctx: Context, a: float, A: TTOp, b: float, B: TTOp, eps: float = -1.0, rmax: int = 0) -> TTOp:
+    h = C.c_void_p()
+    ctx.check(ctx.lib.tt_op_axpby(ctx.h, float(a), A.h, float(b), B.h, float(eps), int(rmax), C.byref(h)))
+    return TTOp(ctx, h)
+
+
+def tt_matvec(ctx: Context, A: TTOp, x: TTVec, scale: float = 1.0, method: int = TT_MV_EXACT,
+              eps: float = -1.0, rmax: int = 0, max_sweeps: int = 4, prec: int = TT_FP64) -> TTVec:
+    h = C.c_void_p()
+    ctx.check(ctx.lib.tt_matvec(ctx.h, A.h, x.h, float(scale), int(method), float(eps), int(rmax),
+                                int(max_sweeps), int(prec), C.byref(h)))
+    return TTVec(ctx, h)
+
+
+def tt_solve_local(ctx: Context, A: TTOp, b: TTVec, x: TTVec, eps: float, rmax: int = 0,
+                   max_sweeps: int = 10, kick: int = 4, prec: int = TT_FP64, allow_noconv: bool = False):
+    sw = C.c_int()
+    dx = C.c_double()
+    rc = ctx.lib.tt_solve_local(ctx.h, A.h, b.h, x.h, float(eps), int(rmax), int(max_sweeps), int(kick),
+                                int(prec), C.byref(sw), C.byref(dx))
+    if not (allow_noconv and rc == TT_ENOCONV):
+        ctx.check(rc)
+    return dict(sweeps=sw.value, rel_change=dx.value, code=rc)
+
+
+class _ProblemArrays:
+    """Keeps the contiguous arrays a TTProblem points into alive."""
+
+    def __init__(self, prob):
+        q = prob.quad
+        self.arrays = dict(
+            sig_t=np.ascontiguousarray(prob.sig_t, np.float64),
+            sig_s=np.ascontiguousarray(prob.sig_s, np.float64),
+            nsf=np.ascontiguousarray(prob.nu_sig_f, np.float64),
+            chi=np.ascontiguousarray(prob.chi, np.float64),
+            mat=np.ascontiguousarray(prob.mat, np.uint8),
+            amu=np.ascontiguousarray(q.amu, np.float64),
+            aeta=np.ascontiguousarray(q.aeta, np.float64),
+            axi=np.ascontiguousarray(q.axi, np.float64),
+            w=np.ascontiguousarray(q.w8, np.float64),
+        )
+        a = self.arrays
+        s = TTProblem()
+        s.l = prob.l
+        for i in range(3):
+            s.side[i] = float(prob.side[i])
+        s.G, s.n_mat = prob.G, prob.n_mat
+        s.sig_t, s.sig_s, s.nu_sig_f, s.chi = _dp(a["sig_t"]), _dp(a["sig_s"]), _dp(a["nsf"]), _dp(a["chi"])
+        s.inv_v = None
+        s.mat = a["mat"].ctypes.data_as(C.POINTER(C.c_uint8))
+        s.n_dir = q.n_per_octant
+        s.amu, s.aeta, s.axi, s.w = _dp(a["amu"]), _dp(a["aeta"]), _dp(a["axi"]), _dp(a["w"])
+        for i in range(6):
+            s.bc[i] = int(prob.bc[i])
+        self.s = s
+
+
+def tt_build_operator(ctx: Context, prob, kind: int, eps_op: float = 1e-12) -> TTOp:
+    pa = _ProblemArrays(prob)
+    h = C.c_void_p()
+    ctx.check(ctx.lib.tt_build_operator(ctx.h, C.byref(pa.s), int(kind), float(eps_op), C.byref(h)))
+    return TTOp(ctx, h)
+
+
+def keig_default_opts() -> KeigOpts:
+    o = KeigOpts()
+    load().keig_default_opts(C.byref(o))
+    return o
+
+
+def keig_fixed_point(ctx: Context, prob, opts: Optional[KeigOpts] = None, want_psi: bool = False,
+                     want_phi: bool = False, allow_noconv: bool = False, psi0=None):
+    """Run the QTT fixed point; returns dict(k, iters, dk, wall_ms, max_rank,
+    k_hist, t_hist, psi (TTVec or None), phi (host array or None), code)."""
+    pa = _ProblemArrays(prob)
+    o = opts if opts is not None else keig_default_opts()
+    keep = None
+    if psi0 is not None:
+        keep = np.ascontiguousarray(np.concatenate([np.asarray(c, np.float64).ravel() for c in psi0]))
+        o.psi0_cores = _dp(keep)
+    res = KeigResult()
+    h = C.c_void_p()
+    phi = np.empty((prob.G, prob.n, prob.n, prob.n)) if want_phi else None
+    rc = ctx.lib.keig_fixed_point(ctx.h, C.byref(pa.s), C.byref(o), C.byref(res),
+                                  C.byref(h) if want_psi else None, _dp(phi) if phi is not None else None)
+    if not (allow_noconv and rc == TT_ENOCONV):
+        ctx.check(rc)
+    it = min(res.iters, 512)
+    return dict(k=res.k, iters=res.iters, dk=res.dk_last, wall_ms=res.wall_ms, max_rank=res.max_rank,
+                k_hist=np.array(res.k_hist[:it]), t_hist=np.array(res.t_hist[:it]),
+                psi=TTVec(ctx, h) if want_psi and h.value else None, phi=phi, code=rc)
+
+
+def tt_scalar_flux(ctx: Context, psi: TTVec, w8) -> TTVec:
+    w = np.ascontiguousarray(w8, np.float64)
+    h = C.c_void_p()
+    ctx.check(ctx.lib.tt_scalar_flux(ctx.h, psi.h, _dp(w), len(w), C.byref(h)))
+    return TTVec(ctx, h)

@@ -1,0 +1,268 @@
+// Construction of the transport operators H, S, F as TT matrices over the
+// modes [G][8][L/8][z bits][y bits][x bits] (Sec. 3.2-3.3 and Algorithm 1).
+//
+// Each operator is a sum of rank-1 terms (tensor products of univariate
+// factors).  Per octant o with cosine signs (sx, sy, sz) (bit set =
+// positive, octant order of Eq. (hat-mu)):
+//   H: I_G (x) E_o (x) diag|mu|  (x) Ip_z (x) Ip_y (x) Dt_x
+//      I_G (x) E_o (x) diag|eta| (x) Ip_z (x) Dt_y (x) Ip_x
+//      I_G (x) E_o (x) diag|xi|  (x) Dt_z (x) Ip_y (x) Ip_x
+//      sum_m diag(sig_t(m)) (x) E_o (x) I (x) M_m^o (Ip_z (x) Ip_y (x) Ip_x)
+//   S: sum_m Sig_s(m)        (x) e_o 1^T (x) 1 w^T (x) M_m^o (Ip_z,noBC (x) Ip_y,noBC (x) Ip_x,noBC)
+//   F: sum_m chi(m) nsf(m)^T (x) e_o 1^T (x) 1 w^T (x) M_m^o (same)
+// with Dt+ = D+, Dt- = -D- (so that mu D^{sign mu} = |mu| Dt), E_o = e_o e_o^T,
+// and M_m^o the diagonal mask of the rows whose upstream cell (cell i-1 along
+// a positive cosine, cell i along a negative one, clamped) is material m.
+// Every n x n spatial factor goes to QTT by Algorithm 1 (reshape, pair the
+// (i_k, j_k) indices, TT-SVD) on the device; the masks are QTT-compressed by
+// TT-SVD of their n^3 values; terms are added and rounded.
+#include <algorithm>
+
+#include "tt.cuh"
+
+namespace tt {
+
+namespace {
+
+std::vector<double> factor_D(int n, double delta, bool pos) {
+  std::vector<double> a((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    a[(size_t)i * n + i] = 1.0 / delta;
+    if (pos && i > 0) a[(size_t)i * n + i - 1] = -1.0 / delta;
+    if (!pos && i + 1 < n) a[(size_t)i * n + i + 1] = -1.0 / delta;
+  }
+  return a;
+}
+
+std::vector<double> factor_Ip(int n, bool pos, bool no_bc) {
+  std::vector<double> a((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    a[(size_t)i * n + i] = 0.5;
+    if (pos && i > 0) a[(size_t)i * n + i - 1] = 0.5;
+    if (!pos && i + 1 < n) a[(size_t)i * n + i + 1] = 0.5;
+  }
+  if (no_bc) {
+    const int row = pos ? 0 : n - 1;
+    for (int j = 0; j < n; ++j) a[(size_t)row * n + j] = 0.0;
+  }
+  return a;
+}
+
+int row_cell(int v, bool pos, int n) {
+  int c = pos ? v - 1 : v;
+  return std::max(0, std::min(c, n - 2));
+}
+
+DBuf upload(Ctx *c, const std::vector<double> &h) {
+  DBuf b(c, h.size());
+  TT_CHECK_CUDA(cudaMemcpyAsync(b.p(), h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  return b;
+}
+
+// Algorithm 1 for one 2^l x 2^l factor: QTT-matrix cores (r, 2, 2, r).
+std::vector<DBuf> qtt_factor(Ctx *c, const std::vector<double> &mat, int l, std::vector<int> &ranks) {
+  const int n = 1 << l;
+  DBuf dm = upload(c, mat);
+  DBuf perm(c, (size_t)n * n);
+  std::vector<int> shape(2 * l, 2), p(2 * l);
+  for (int k = 0; k < l; ++k) {
+    p[2 * k] = k;          // i_k
+    p[2 * k + 1] = l + k;  // j_k
+  }
+  permute(c, dm.p(), perm.p(), 2 * l, shape.data(), p.data());
+  std::vector<int> modes(l, 4);
+  TT t = tt_svd_dense(c, perm.p(), modes, 1e-14, 0);
+  ranks = t.r;
+  return std::move(t.core);
+}
+
+__global__ void diag_times_op_kernel(const double *__restrict__ mk, int rc0, int rc1,
+                                     const double *__restrict__ S, int Rs0, int Rs1, double *__restrict__ out) {
+  // out[(a,al), i, j, (b,be)] = mk[a, i, b] * S[al, i, j, be]
+  const long long tot = (long long)rc0 * Rs0 * 4 * rc1 * Rs1;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    long long rem = e;
+    const int be = (int)(rem % Rs1);
+    rem /= Rs1;
+    const int b = (int)(rem % rc1);
+    rem /= rc1;
+    const int j = (int)(rem % 2);
+    rem /= 2;
+    const int i = (int)(rem % 2);
+    rem /= 2;
+    const int al = (int)(rem % Rs0);
+    const int a = (int)(rem / Rs0);
+    out[e] = mk[((long long)a * 2 + i) * rc1 + b] * S[(((long long)al * 2 + i) * 2 + j) * Rs1 + be];
+  }
+}
+
+struct Term {
+  std::vector<std::vector<double>> head;  // G x G, 8 x 8, nd x nd factors
+  int fz, fy, fx;                         // indices into the QTT factor list
+  int mask;                               // -1 or index into the mask list
+};
+
+}  // namespace
+
+TT build_operator(Ctx *c, const tt_problem *p, int kind, double eps_op) {
+  const int l = p->l, n = 1 << l, G = p->G, nd = p->n_dir, nm = p->n_mat;
+  const double dx = p->side[0] / (n - 1), dy = p->side[1] / (n - 1), dz = p->side[2] / (n - 1);
+  const int d = 3 + 3 * l;
+  // ---- QTT of the distinct spatial factors
+  std::vector<std::vector<double>> facs;
+  std::vector<std::vector<DBuf>> qf;
+  std::vector<std::vector<int>> qr;
+  auto add_factor = [&](std::vector<double> f) {
+    facs.push_back(std::move(f));
+    std::vector<int> rk;
+    qf.push_back(qtt_factor(c, facs.back(), l, rk));
+    qr.push_back(rk);
+    return (int)facs.size() - 1;
+  };
+  // index: [axis][pos] for D, Ip, IpNoBC
+  int iD[3][2], iIp[2], iIpN[2];
+  const double del[3] = {dx, dy, dz};
+  for (int pos = 0; pos < 2; ++pos) {
+    iIp[pos] = add_factor(factor_Ip(n, pos, false));
+    iIpN[pos] = add_factor(factor_Ip(n, pos, true));
+    for (int a = 0; a < 3; ++a) iD[a][pos] = add_factor(factor_D(n, del[a], pos));
+  }
+  // ---- material masks per (octant, material) in QTT (only when heterogeneous)
+  std::vector<TT> masks;
+  std::vector<int> mask_index((size_t)8 * nm, -1);
+  if (nm > 1) {
+    const int nc = n - 1;
+    std::vector<double> mv((size_t)n * n * n);
+    std::vector<int> mode3(3 * l, 2);
+    for (int o = 0; o < 8; ++o) {
+      const bool px = o & 1, py = o & 2, pz = o & 4;
+      for (int m = 0; m < nm; ++m) {
+        size_t cnt = 0;
+        for (int k = 0; k < n; ++k)
+          for (int j = 0; j < n; ++j)
+            for (int i = 0; i < n; ++i) {
+              const int mat = p->mat[((size_t)row_cell(k, pz, n) * nc + row_cell(j, py, n)) * nc + row_cell(i, px, n)];
+              const double v = (mat == m) ? 1.0 : 0.0;
+              mv[((size_t)k * n + j) * n + i] = v;
+              cnt += (mat == m);
+            }
+        if (!cnt) continue;
+        DBuf dmv = upload(c, mv);
+        masks.push_back(tt_svd_dense(c, dmv.p(), mode3, 1e-14, 0));
+        mask_index[(size_t)o * nm + m] = (int)masks.size() - 1;
+      }
+    }
+  }
+  // ---- the rank-1 terms of the requested operator
+  std::vector<Term> terms;
+  auto eye = [](int k) {
+    std::vector<double> a((size_t)k * k, 0.0);
+    for (int i = 0; i < k; ++i) a[(size_t)i * k + i] = 1.0;
+    return a;
+  };
+  auto diag = [](const double *v, int k) {
+    std::vector<double> a((size_t)k * k, 0.0);
+    for (int i = 0; i < k; ++i) a[(size_t)i * k + i] = v[i];
+    return a;
+  };
+  for (int o = 0; o < 8; ++o) {
+    const int px = (o & 1) ? 1 : 0, py = (o & 2) ? 1 : 0, pz = (o & 4) ? 1 : 0;
+    std::vector<double> E(64, 0.0), Intg(64, 0.0);
+    E[o * 8 + o] = 1.0;
+    for (int j = 0; j < 8; ++j) Intg[o * 8 + j] = 1.0;
+    if (kind == TT_OP_H) {
+      terms.push_back({{eye(G), E, diag(p->amu, nd)}, iIp[pz], iIp[py], iD[0][px], -1});
+      terms.push_back({{eye(G), E, diag(p->aeta, nd)}, iIp[pz], iD[1][py], iIp[px], -1});
+      terms.push_back({{eye(G), E, diag(p->axi, nd)}, iD[2][pz], iIp[py], iIp[px], -1});
+      for (int m = 0; m < nm; ++m) {
+        const int mi = nm > 1 ? mask_index[(size_t)o * nm + m] : -1;
+        if (nm > 1 && mi < 0) continue;
+        terms.push_back({{diag(p->sig_t + (size_t)m * G, G), E, eye(nd)}, iIp[pz], iIp[py], iIp[px], mi});
+      }
+    } else {
+      std::vector<double> dirm((size_t)nd * nd);
+      for (int a = 0; a < nd; ++a)
+        for (int b = 0; b < nd; ++b) dirm[(size_t)a * nd + b] = p->w[b];
+      for (int m = 0; m < nm; ++m) {
+        const int mi = nm > 1 ? mask_index[(size_t)o * nm + m] : -1;
+        if (nm > 1 && mi < 0) continue;
+        std::vector<double> gm((size_t)G * G);
+        bool nonzero = false;
+        for (int a = 0; a < G; ++a)
+          for (int b = 0; b < G; ++b) {
+            const double v = kind == TT_OP_S ? p->sig_s[((size_t)m * G + a) * G + b]
+                                             : p->chi[(size_t)m * G + a] * p->nu_sig_f[(size_t)m * G + b];
+            gm[(size_t)a * G + b] = v;
+            nonzero |= v != 0.0;
+          }
+        if (!nonzero) continue;
+        terms.push_back({{gm, Intg, dirm}, iIpN[pz], iIpN[py], iIpN[px], mi});
+      }
+    }
+  }
+  // ---- assemble each term as a TT matrix and accumulate with rounding
+  std::vector<int> mo(d), mi(d);
+  mo[0] = mi[0] = G;
+  mo[1] = mi[1] = 8;
+  mo[2] = mi[2] = nd;
+  for (int k = 3; k < d; ++k) mo[k] = mi[k] = 2;
+  TT acc;
+  bool have = false;
+  int pending = 0;
+  for (const Term &t : terms) {
+    TT x;
+    x.d = d;
+    x.mo = mo;
+    x.mi = mi;
+    x.n.resize(d);
+    for (int k = 0; k < d; ++k) x.n[k] = mo[k] * mi[k];
+    x.r.assign(d + 1, 1);
+    x.core.resize(d);
+    for (int k = 0; k < 3; ++k) x.core[k] = upload(c, t.head[k]);
+    const int fidx[3] = {t.fz, t.fy, t.fx};
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < l; ++b) {
+        const int k = 3 + a * l + b;
+        x.r[k] = qr[fidx[a]][b];
+        x.r[k + 1] = qr[fidx[a]][b + 1];
+        x.core[k].alloc(c, x.csize(k));
+        copy(c, x.core[k].p(), qf[fidx[a]][b].p(), x.csize(k));
+      }
+    if (t.mask >= 0) {
+      // M (Ip (x) Ip (x) Ip): core-wise product with the diagonal mask TT
+      const TT &mk = masks[t.mask];
+      for (int q = 0; q < 3 * l; ++q) {
+        const int k = 3 + q;
+        const int rc0 = mk.r[q], rc1 = mk.r[q + 1], Rs0 = x.r[k], Rs1 = x.r[k + 1];
+        DBuf out(c, (size_t)rc0 * Rs0 * 4 * rc1 * Rs1);
+        const long long tot = (long long)rc0 * Rs0 * 4 * rc1 * Rs1;
+        diag_times_op_kernel<<<(unsigned)std::min<long long>((tot + 255) / 256, 4096), 256, 0, c->stream>>>(
+            mk.core[q].p(), rc0, rc1, x.core[k].p(), Rs0, Rs1, out.p());
+        c->count();
+        TT_CHECK_CUDA(cudaGetLastError());
+        x.core[k] = std::move(out);
+      }
+      for (int q = 0; q <= 3 * l; ++q) x.r[3 + q] = (q == 0 || q == 3 * l) ? x.r[3 + q] : mk.r[q] * x.r[3 + q];
+      // the bond between the head cores and the first spatial core keeps rank 1
+      x.r[3] = 1;
+      x.r[d] = 1;
+      round(c, x, 1e-14, 0);
+    }
+    if (!have) {
+      acc = std::move(x);
+      have = true;
+    } else {
+      acc = add(c, 1.0, acc, 1.0, x);
+      if (++pending >= 4) {
+        round(c, acc, eps_op, 0);
+        pending = 0;
+      }
+    }
+  }
+  TT_REQUIRE(have, "build_operator: operator has no terms");
+  round(c, acc, eps_op, 0);
+  return acc;
+}
+
+}  // namespace tt

@@ -1,0 +1,573 @@
+// extern "C" boundary of libkeig_tt (declared in include/keig.h) and the
+// k-eigenvalue fixed point of Eq. (TT_k_eff_fixed_points).
+#include <chrono>
+
+#include "tt.cuh"
+
+struct tt_ctx {
+  tt::Ctx c;
+};
+struct tt_vec {
+  tt::Ctx *owner;
+  tt::TT t;
+};
+struct tt_op {
+  tt::Ctx *owner;
+  tt::TTOp op;
+};
+
+namespace {
+
+template <class F>
+int guarded(tt_ctx *ctx, F &&f) {
+  if (!ctx) return TT_EINVAL;
+  try {
+    f();
+    ctx->c.err.clear();
+    return TT_OK;
+  } catch (const tt::Error &e) {
+    ctx->c.err = e.what();
+    return e.code;
+  } catch (const std::bad_alloc &) {
+    ctx->c.err = "host allocation failed";
+    return TT_ENOMEM;
+  } catch (const std::exception &e) {
+    ctx->c.err = e.what();
+    return TT_EINVAL;
+  }
+}
+
+std::vector<int> to_vec(const int *p, int n) { return std::vector<int>(p, p + n); }
+
+void check_finite_host(const double *p, size_t n, const char *what) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(p[i])) throw tt::Error(TT_EINVAL, std::string("non-finite value in ") + what);
+}
+
+tt::TT make_tt(tt::Ctx *c, int d, const int *n, const int *r, const double *cores, int on_dev) {
+  TT_REQUIRE(d >= 1 && d <= 256 && n && r, "tt: bad shape arguments");
+  std::vector<int> nv = to_vec(n, d), rv = to_vec(r, d + 1);
+  TT_REQUIRE(rv[0] == 1 && rv[d] == 1, "tt: r[0] and r[d] must be 1");
+  for (int k = 0; k < d; ++k) TT_REQUIRE(nv[k] >= 1 && rv[k] >= 1 && rv[k] <= 4096, "tt: bad mode or rank");
+  tt::TT x = tt::tt_zeros(c, nv, rv);
+  if (cores) {
+    size_t off = 0;
+    for (int k = 0; k < d; ++k) {
+      const size_t sz = x.csize(k);
+      if (!on_dev) check_finite_host(cores + off, sz, "TT cores");
+      TT_CHECK_CUDA(cudaMemcpyAsync(x.core[k].p(), cores + off, sz * sizeof(double),
+                                    on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+      off += sz;
+    }
+    c->sync();
+  }
+  return x;
+}
+
+void get_cores(tt::Ctx *c, const tt::TT &x, double *dst, int on_dev) {
+  TT_REQUIRE(dst, "null destination");
+  size_t off = 0;
+  for (int k = 0; k < x.d; ++k) {
+    const size_t sz = x.csize(k);
+    TT_CHECK_CUDA(cudaMemcpyAsync(dst + off, x.core[k].p(), sz * sizeof(double),
+                                  on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    off += sz;
+  }
+  c->sync();
+}
+
+void validate_problem(const tt_problem *p) {
+  TT_REQUIRE(p, "null problem");
+  TT_REQUIRE(p->l >= 1 && p->l <= 10, "problem: l must be in [1, 10]");
+  TT_REQUIRE(p->G >= 1 && p->G <= 4096, "problem: bad G");
+  TT_REQUIRE(p->n_mat >= 1 && p->n_mat <= 255, "problem: bad n_mat");
+  TT_REQUIRE(p->n_dir >= 1 && p->n_dir <= 4096, "problem: bad n_dir");
+  TT_REQUIRE(p->sig_t && p->sig_s && p->nu_sig_f && p->chi && p->mat && p->amu && p->aeta && p->axi && p->w,
+             "problem: null table");
+  for (int f = 0; f < 6; ++f) TT_REQUIRE(p->bc[f] == 0, "problem: only vacuum faces (bc = 0) are supported");
+  for (int a = 0; a < 3; ++a) TT_REQUIRE(p->side[a] > 0 && std::isfinite(p->side[a]), "problem: bad side");
+  const size_t G = p->G, nm = p->n_mat, nd = p->n_dir;
+  check_finite_host(p->sig_t, nm * G, "sig_t");
+  check_finite_host(p->sig_s, nm * G * G, "sig_s");
+  check_finite_host(p->nu_sig_f, nm * G, "nu_sig_f");
+  check_finite_host(p->chi, nm * G, "chi");
+  check_finite_host(p->amu, nd, "amu");
+  check_finite_host(p->aeta, nd, "aeta");
+  check_finite_host(p->axi, nd, "axi");
+  check_finite_host(p->w, nd, "w");
+  const size_t nc = ((size_t)1 << p->l) - 1;
+  for (size_t i = 0; i < nc * nc * nc; ++i)
+    TT_REQUIRE(p->mat[i] < p->n_mat, "problem: material index out of range");
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *tt_version(void) { return "keig-tt 0.1 (sm_103a, FP64)"; }
+
+int tt_ctx_create(tt_ctx **out, void *stream) {
+  if (!out) return TT_EINVAL;
+  *out = nullptr;
+  tt_ctx *ctx = new (std::nothrow) tt_ctx();
+  if (!ctx) return TT_ENOMEM;
+  int rc = guarded(ctx, [&] {
+    int ndev = 0;
+    TT_CHECK_CUDA(cudaGetDeviceCount(&ndev));
+    TT_REQUIRE(ndev > 0, "no CUDA device");
+    TT_CHECK_CUDA(cudaGetDevice(&ctx->c.device));
+    cudaDeviceProp prop;
+    TT_CHECK_CUDA(cudaGetDeviceProperties(&prop, ctx->c.device));
+    ctx->c.sm_count = prop.multiProcessorCount;
+    ctx->c.stream = (cudaStream_t)stream;
+    // keep freed blocks in the stream-ordered pool
+    cudaMemPool_t pool;
+    TT_CHECK_CUDA(cudaDeviceGetDefaultMemPool(&pool, ctx->c.device));
+    uint64_t thr = UINT64_MAX;
+    TT_CHECK_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
+    TT_CHECK_CUDA(cudaMalloc(&ctx->c.d_scalar, 64 * sizeof(double)));
+    TT_CHECK_CUDA(cudaMallocHost(&ctx->c.h_pinned, 4096 * sizeof(double)));
+  });
+  if (rc != TT_OK) {
+    delete ctx;
+    return rc == TT_EINVAL ? TT_ECUDA : rc;
+  }
+  *out = ctx;
+  return TT_OK;
+}
+
+int tt_ctx_destroy(tt_ctx *ctx) {
+  if (!ctx) return TT_EINVAL;
+  cudaStreamSynchronize(ctx->c.stream);
+  ctx->c.ws_gemm.release();
+  for (auto &s : ctx->c.scratch) s.release();
+  cudaStreamSynchronize(ctx->c.stream);
+  if (ctx->c.d_scalar) cudaFree(ctx->c.d_scalar);
+  if (ctx->c.h_pinned) cudaFreeHost(ctx->c.h_pinned);
+  delete ctx;
+  return TT_OK;
+}
+
+const char *tt_last_error(const tt_ctx *ctx) { return ctx ? ctx->c.err.c_str() : "null context"; }
+
+int tt_ctx_counters(tt_ctx *ctx, int64_t *launches, double *flops) {
+  if (!ctx) return TT_EINVAL;
+  if (launches) *launches = ctx->c.launches;
+  if (flops) *flops = ctx->c.flops;
+  return TT_OK;
+}
+
+int tt_ctx_reset_counters(tt_ctx *ctx) {
+  if (!ctx) return TT_EINVAL;
+  ctx->c.launches = 0;
+  ctx->c.flops = 0.0;
+  return TT_OK;
+}
+
+// ---------------------------------------------------------------- vectors
+int tt_vec_create(tt_ctx *ctx, int d, const int *n, const int *r, const double *cores, int on_dev, tt_vec **out) {
+  return guarded(ctx, [&] {
+    TT_REQUIRE(out, "null out");
+    tt::TT x = make_tt(&ctx->c, d, n, r, cores, on_dev);
+    *out = new tt_vec{&ctx->c, std::move(x)};
+  });
+}
+
+int tt_vec_destroy(tt_vec *x) {
+  if (!x) return TT_EINVAL;
+  delete x;
+  return TT_OK;
+}
+
+int tt_vec_shape(const tt_vec *x, int *d, int *n, int *r) {
+  if (!x || !d) return TT_EINVAL;
+  *d = x->t.d;
+  if (n)
+    for (int k = 0; k < x->t.d; ++k) n[k] = x->t.n[k];
+  if (r)
+    for (int k = 0; k <= x->t.d; ++k) r[k] = x->t.r[k];
+  return TT_OK;
+}
+
+int tt_vec_numel(const tt_vec *x, size_t *count) {
+  if (!x || !count) return TT_EINVAL;
+  *count = x->t.numel();
+  return TT_OK;
+}
+
+int tt_vec_get_cores(tt_ctx *ctx, const tt_vec *x, double *dst, int on_dev) {
+  return guarded(ctx, [&] {
+    TT_REQUIRE(x, "null vector");
+    get_cores(&ctx->c, x->t, dst, on_dev);
+  });
+}
+
+int tt_vec_to_dense(tt_ctx *ctx, const tt_vec *x, double *dst, size_t len) {
+  return guarded(ctx, [&] {
+    TT_REQUIRE(x && dst, "null argument");
+    tt::to_dense(&ctx->c, x->t, dst, len);
+    ctx->c.sync();
+  });
+}
+
+int tt_vec_axpby(tt_ctx *ctx, double a, const tt_vec *x, double b, tt_vec *y) {
+  return guarded(ctx, [&] {
+    TT_REQUIRE(x && y, "null vector");
+    y->t = tt::add(&ctx->c, a, x->t, b, y->t);
+  });
+}
+
+int tt_vec_scale(tt_ctx *ctx, tt_vec *x, double a) {
+  return guarded(ctx, [&] {
+    TT_REQUIRE(x, "null vector");
+    tt::scale(&ctx->c, x->t, a);
+  });
+}
+
+int tt_vec_dot(tt_ctx *ctx, const tt_vec *x, const tt_vec *y, double *out) {
+  return guarded(ctx, [&] {
+    TT_REQUIRE(x && y && out, "null argument");
+    *out = tt::dot(&ctx->c, x->t, y->t);
+  });
+}
+
+int tt_vec_norm(tt_ctx *ctx, const tt_vec *x, double *out) {
+  return guarded(ctx, [&] {
+    TT_REQUIRE(x && out, "null argument");
+    *out = tt::norm(&ctx->c, x->t);
+  });
+}
+
+int tt_vec_sum(tt_ctx *ctx, const tt_vec *x, double *out) {
+  return guarded(ctx, [&] {
+    TT_REQUIRE(x && out, "null argument");
+    *out = tt::sum(&ctx->c, x->t);
+  });
+}
+
+int tt_round(tt_ctx *ctx, tt_vec *x, double eps, int rmax) {
+  return guarded(ctx, [&] {
+    TT_REQUIRE(x, "null vector");
+    TT_REQUIRE(eps >= 0 && std::isfinite(eps), "tt_round: eps must be finite and >= 0");
+    TT_REQUIRE(x->t.max_rank() <= 512, "tt_round: rank above 512");
+    tt::round(&ctx->c, x->t, eps, rmax);
+  });
+}
+
+// ---------------------------------------------------------------- operators
+int tt_op_create(tt_ctx *ctx, int d, const int *m, const int *n, const int *R, const double *cores, int on_dev,
+                 tt_op **out) {
+  return guarded(ctx, [&] {
+    TT_REQUIRE(out && m && n, "null argument");
+    std::vector<int> mn(d);
+    for (int k = 0; k < d; ++k) {
+      TT_REQUIRE(m[k] >= 1 && n[k] >= 1, "tt_op: bad mode");
+      mn[k] = m[k] * n[k];
+    }
+    tt::TT x = make_tt(&ctx->c, d, mn.data(), R, cores, on_dev);
+    x.mo = to_vec(m, d);
+    x.mi = to_vec(n, d);
+    tt_op *A = new tt_op{&ctx->c, {}};
+    A->op.t = std::move(x);
+    *out = A;
+  });
+}
+
+int tt_op_destroy(tt_op *A) {
+  if (!A) return TT_EINVAL;
+  delete A;
+  return TT_OK;
+}
+
+int tt_op_shape(const tt_op *A, int *d, int *m, int *n, int *R) {
+  if (!A || !d) return TT_EINVAL;
+  const tt::TT &t = A->op.t;
+  *d = t.d;
+  for (int k = 0; k < t.d; ++k) {
+    if (m) m[k] = t.mo[k];
+    if (n) n[k] = t.mi[k];
+  }
+  if (R)
+    for (int k = 0; k <= t.d; ++k) R[k] = t.r[k];
+  return TT_OK;
+}
+
+int tt_op_numel(const tt_op *A, size_t *count) {
+  if (!A || !count) return TT_EINVAL;
+  *count = A->op.t.numel();
+  return TT_OK;
+}
+
+int tt_op_get_cores(tt_ctx *ctx, const tt_op *A, double *dst, int on_dev) {
+  return guarded(ctx, [&] {
+    TT_REQUIRE(A, "null operator");
+    get_cores(&ctx->c, A->op.t, dst, on_dev);
+  });
+}
+
+int tt_op_axpby(tt_ctx *ctx, double a, const tt_op *A, double b, const tt_op *B, double eps, int rmax,
+                tt_op **out) {
+  return guarded(ctx, [&] {
+    TT_REQUIRE(A && B && out, "null argument");
+    for (int k = 0; k < A->op.t.d; ++k)
+      TT_REQUIRE(A->op.t.mo[k] == B->op.t.mo[k] && A->op.t.mi[k] == B->op.t.mi[k], "tt_op_axpby: modes differ");
+    tt::TT s = tt::add(&ctx->c, a, A->op.t, b, B->op.t);
+    if (eps >= 0) tt::round(&ctx->c, s, eps, rmax);
+    tt_op *C = new tt_op{&ctx->c, {}};
+    C->op.t = std::move(s);
+    *out = C;
+  });
+}
+
+int tt_build_operator(tt_ctx *ctx, const tt_problem *prob, tt_op_kind kind, double eps_op, tt_op **out) {
+  return guarded(ctx, [&] {
+    TT_REQUIRE(out, "null out");
+    validate_problem(prob);
+    TT_REQUIRE(kind == TT_OP_H || kind == TT_OP_S || kind == TT_OP_F, "tt_build_operator: bad kind");
+    TT_REQUIRE(eps_op >= 0 && eps_op < 1, "tt_build_operator: bad eps_op");
+    tt_op *A = new tt_op{&ctx->c, {}};
+    try {
+      A->op.t = tt::build_operator(&ctx->c, prob, (int)kind, eps_op);
+    } catch (...) {
+      delete A;
+      throw;
+    }
+    *out = A;
+  });
+}
+
+// ---------------------------------------------------------------- products and solves
+int tt_matvec(tt_ctx *ctx, const tt_op *A, const tt_vec *x, double scale, int method, double eps, int rmax,
+              int max_sweeps, tt_prec prec, tt_vec **y) {
+  return guarded(ctx, [&] {
+    TT_REQUIRE(A && x && y, "null argument");
+    TT_REQUIRE(prec == TT_FP64, "tt_matvec: only TT_FP64 is built");
+    TT_REQUIRE(std::isfinite(scale), "tt_matvec: non-finite scale");
+    tt::Ctx *c = &ctx->c;
+    if (method == TT_MV_EXACT) {
+      tt::TT r = tt::matvec_exact(c, A->op.t, x->t);
+      if (eps >= 0) {
+        TT_REQUIRE(r.max_rank() <= 512, "tt_matvec: product rank above 512, use TT_MV_AMEN");
+        tt::round(c, r, eps, rmax);
+      }
+      tt::scale(c, r, scale);
+      *y = new tt_vec{c, std::move(r)};
+    } else if (method == TT_MV_AMEN) {
+      TT_REQUIRE(eps > 0, "tt_matvec: AMEn needs eps > 0");
+      tt_op *Am = const_cast<tt_op *>(A);
+      std::vector<int> outn(A->op.t.d);
+      for (int k = 0; k < A->op.t.d; ++k) outn[k] = A->op.t.mo[k];
+      tt::TT yy = tt::tt_ones(c, outn);
+      tt::amen_mv(c, Am->op, x->t, yy, eps, rmax, std::max(1, max_sweeps), 4, 12345, nullptr);
+      tt::scale(c, yy, scale);
+      *y = new tt_vec{c, std::move(yy)};
+    } else {
+      throw tt::Error(TT_EINVAL, "tt_matvec: unknown method");
+    }
+  });
+}
+
+int tt_solve_local(tt_ctx *ctx, const tt_op *A, const tt_vec *b, tt_vec *x, double eps, int rmax, int max_sweeps,
+                   int kick, tt_prec prec, int *sweeps_done, double *rel_change) {
+  int conv = 1;
+  int rc = guarded(ctx, [&] {
+    TT_REQUIRE(A && b && x, "null argument");
+    TT_REQUIRE(prec == TT_FP64, "tt_solve_local: only TT_FP64 is built");
+    TT_REQUIRE(eps > 0 && eps < 1, "tt_solve_local: eps in (0, 1)");
+    TT_REQUIRE(max_sweeps >= 1 && kick >= 0, "tt_solve_local: bad sweeps/kick");
+    tt_op *Am = const_cast<tt_op *>(A);
+    tt::SolveStats st;
+    tt::amen_solve(&ctx->c, Am->op, b->t, x->t, eps, rmax, max_sweeps, kick, 4242, &st);
+    if (sweeps_done) *sweeps_done = st.sweeps;
+    if (rel_change) *rel_change = st.max_dx;
+    conv = st.max_dx < eps;
+  });
+  if (rc == TT_OK && !conv) {
+    ctx->c.err = "tt_solve_local: sweep limit reached before the local changes fell below eps";
+    return TT_ENOCONV;
+  }
+  return rc;
+}
+
+int tt_scalar_flux(tt_ctx *ctx, const tt_vec *psi, const double *w_host, int n_dir, tt_vec **phi) {
+  return guarded(ctx, [&] {
+    TT_REQUIRE(psi && w_host && phi, "null argument");
+    const tt::TT &x = psi->t;
+    TT_REQUIRE(x.d >= 4 && x.n[1] == 8 && x.n[2] == n_dir, "tt_scalar_flux: expected cores [G][8][L/8][...]");
+    tt::Ctx *c = &ctx->c;
+    std::vector<double> ones(8, 1.0);
+    tt::DBuf d1(c, 8), dw(c, n_dir);
+    TT_CHECK_CUDA(cudaMemcpyAsync(d1.p(), ones.data(), 8 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    TT_CHECK_CUDA(cudaMemcpyAsync(dw.p(), w_host, n_dir * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    const int r1 = x.r[1], r2 = x.r[2], r3 = x.r[3];
+    tt::DBuf A(c, (size_t)r1 * r2), B(c, (size_t)r2 * r3), W(c, (size_t)r1 * r3);
+    tt::contract_mode(c, x.core[1].p(), r1, 8, r2, d1.p(), A.p());
+    tt::contract_mode(c, x.core[2].p(), r2, n_dir, r3, dw.p(), B.p());
+    tt::gemm(c, false, false, r1, r3, r2, 1.0, A.p(), r2, 0, B.p(), r3, 0, 0.0, W.p(), r3, 0);
+    tt::TT y;
+    y.d = x.d - 2;
+    y.n.push_back(x.n[0]);
+    y.r.push_back(1);
+    y.r.push_back(r3);
+    y.core.resize(y.d);
+    y.core[0].alloc(c, (size_t)x.n[0] * r3);
+    tt::gemm(c, false, false, x.n[0], r3, r1, 1.0, x.core[0].p(), r1, 0, W.p(), r3, 0, 0.0, y.core[0].p(), r3, 0);
+    for (int k = 3; k < x.d; ++k) {
+      y.n.push_back(x.n[k]);
+      y.r.push_back(x.r[k + 1]);
+      y.core[k - 2].alloc(c, x.csize(k));
+      tt::copy(c, y.core[k - 2].p(), x.core[k].p(), x.csize(k));
+    }
+    c->sync();
+    *phi = new tt_vec{c, std::move(y)};
+  });
+}
+
+int keig_default_opts(keig_opts *o) {
+  if (!o) return TT_EINVAL;
+  o->eps = 1e-7;
+  o->rmax = 64;
+  o->tol_k = 1e-9;
+  o->tol_psi = 1e-5;
+  o->max_iter = 400;
+  o->solve_sweeps = 2;
+  o->mv_sweeps = 2;
+  o->kick = 4;
+  o->scheme = 0;
+  o->prec = TT_FP64;
+  o->eps_op = 1e-12;
+  o->psi0_cores = nullptr;
+  return TT_OK;
+}
+
+int keig_fixed_point(tt_ctx *ctx, const tt_problem *prob, const keig_opts *opts, keig_result *out,
+                     tt_vec **psi_out, double *phi_out) {
+  int conv = 0;
+  int rc = guarded(ctx, [&] {
+    TT_REQUIRE(opts && out, "null argument");
+    validate_problem(prob);
+    TT_REQUIRE(opts->prec == TT_FP64, "keig_fixed_point: only TT_FP64 is built");
+    TT_REQUIRE(opts->eps > 0 && opts->eps < 1 && opts->max_iter >= 1, "keig_fixed_point: bad eps/max_iter");
+    TT_REQUIRE(opts->scheme == 0 || opts->scheme == 1, "keig_fixed_point: scheme must be 0 or 1");
+    using clk = std::chrono::steady_clock;
+    const auto t0 = clk::now();
+    auto ms = [&] { return std::chrono::duration<double, std::milli>(clk::now() - t0).count(); };
+    tt::Ctx *c = &ctx->c;
+    memset(out, 0, sizeof(*out));
+    // operators (Sec. 3.2-3.3)
+    tt::TTOp H, S, F, LHS, RHS;
+    H.t = tt::build_operator(c, prob, TT_OP_H, opts->eps_op);
+    S.t = tt::build_operator(c, prob, TT_OP_S, opts->eps_op);
+    F.t = tt::build_operator(c, prob, TT_OP_F, opts->eps_op);
+    // f = F^T 1, so that sum(F Psi) = <f, Psi>
+    tt::TT ones = tt::tt_ones(c, F.t.mi);
+    tt::TT FT = tt::transpose_op(c, F.t);
+    tt::TT f = tt::matvec_exact(c, FT, ones);
+    tt::round(c, f, 1e-13, 0);
+    const int d = H.t.d;
+    // the RHS operator: scheme 0: S (+) F (first-core block of F rescaled by 1/k)
+    //                   scheme 1: F / k, LHS = H - S
+    int rS = S.t.r[1];
+    if (opts->scheme == 0) {
+      RHS.t = tt::add(c, 1.0, S.t, 1.0, F.t);
+      LHS.t = std::move(H.t);
+    } else {
+      RHS.t = tt::tt_clone(c, F.t);
+      LHS.t = tt::add(c, 1.0, H.t, -1.0, S.t);
+      tt::round(c, LHS.t, opts->eps_op, 0);
+      H.t = tt::TT();
+    }
+    // initial guess: positive rank-1 TT
+    std::vector<int> modes = LHS.t.mi;
+    tt::TT psi = tt::tt_ones(c, modes);
+    if (opts->psi0_cores) {
+      size_t off = 0;
+      for (int k = 0; k < d; ++k) {
+        check_finite_host(opts->psi0_cores + off, modes[k], "psi0");
+        TT_CHECK_CUDA(cudaMemcpyAsync(psi.core[k].p(), opts->psi0_cores + off, modes[k] * sizeof(double),
+                                      cudaMemcpyHostToDevice, c->stream));
+        off += modes[k];
+      }
+    }
+    double s = tt::dot(c, f, psi);
+    TT_REQUIRE(s != 0.0 && std::isfinite(s), "keig: initial guess has zero production");
+    tt::scale(c, psi, 1.0 / s);
+    double k = 1.0;  // scale of the F block currently stored in RHS
+    double k_in_op = 1.0;
+    tt::TT B = tt::tt_clone(c, psi);
+    int it = 0;
+    double dk = 1e300;
+    for (it = 0; it < opts->max_iter; ++it) {
+      // RHS operator for this k
+      const double fac = k_in_op / k;  // rescale the F part by (1/k) / (1/k_in_op)
+      if (opts->scheme == 0) {
+        // F's first core occupies columns [rS, rS + rF) of the (1, G*G, rS + rF) first core
+        const int rtot = RHS.t.r[1], rF = rtot - rS, ncol = RHS.t.n[0];
+        tt::copy2d(c, RHS.t.core[0].p() + rS, rtot, RHS.t.core[0].p() + rS, rtot, ncol, rF, fac);
+        if (RHS.prepared) {
+          RHS.prepared = false;
+          RHS.a_ajib.clear();
+          RHS.a_jbai.clear();
+        }
+      } else {
+        tt::scale(c, RHS.t.core[0].p(), RHS.t.csize(0), fac);
+        RHS.prepared = false;
+        RHS.a_ajib.clear();
+        RHS.a_jbai.clear();
+      }
+      k_in_op = k;
+      tt::SolveStats mst, sst;
+      tt::amen_mv(c, RHS, psi, B, opts->eps, opts->rmax, opts->mv_sweeps, opts->kick, 1000 + it, &mst);
+      tt::TT psi_new = tt::tt_clone(c, psi);
+      tt::amen_solve(c, LHS, B, psi_new, opts->eps, opts->rmax, opts->solve_sweeps, opts->kick, 5000 + it, &sst);
+      const double sn = tt::dot(c, f, psi_new);
+      if (!std::isfinite(sn) || sn == 0.0) throw tt::Error(TT_ENONFINITE, "keig: production became zero or non-finite");
+      const double kn = k * sn;
+      tt::scale(c, psi_new, 1.0 / sn);
+      // relative change of Psi: ||a - b||^2 = <a,a> + <b,b> - 2<a,b>
+      const double aa = tt::dot(c, psi_new, psi_new), bb = tt::dot(c, psi, psi), ab = tt::dot(c, psi_new, psi);
+      const double dpsi = std::sqrt(std::max(aa + bb - 2 * ab, 0.0) / std::max(aa, 1e-300));
+      dk = std::fabs(kn - k) / std::fabs(kn);
+      k = kn;
+      psi = std::move(psi_new);
+      if (it < 512) {
+        out->k_hist[it] = k;
+        out->t_hist[it] = ms();
+      }
+      if (dk < opts->tol_k && dpsi < opts->tol_psi) {
+        ++it;
+        conv = 1;
+        break;
+      }
+    }
+    out->k = k;
+    out->iters = std::min(it, opts->max_iter);
+    out->dk_last = dk;
+    out->max_rank = psi.max_rank();
+    if (phi_out) {
+      // scalar flux on the vertices, dense
+      const int n = 1 << prob->l;
+      tt_vec tmp{c, std::move(psi)};
+      tt_vec *phi = nullptr;
+      int r2 = tt_scalar_flux(ctx, &tmp, prob->w, prob->n_dir, &phi);
+      if (r2 != TT_OK) throw tt::Error(r2, ctx->c.err);
+      const size_t len = (size_t)prob->G * n * n * n;
+      tt::DBuf dst(c, len);
+      tt::to_dense(c, phi->t, dst.p(), len);
+      TT_CHECK_CUDA(cudaMemcpyAsync(phi_out, dst.p(), len * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      c->sync();
+      tt_vec_destroy(phi);
+      psi = std::move(tmp.t);
+    }
+    if (psi_out) *psi_out = new tt_vec{c, std::move(psi)};
+    c->sync();
+    out->wall_ms = ms();
+  });
+  if (rc == TT_OK && !conv) {
+    ctx->c.err = "keig_fixed_point: max_iter reached";
+    return TT_ENOCONV;
+  }
+  return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,139 @@
+// Internal declarations shared by the translation units of libkeig_tt.
+// Everything here is FP64; all device work runs on the context stream.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <stdexcept>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/keig.h"
+
+namespace tt {
+
+// ----------------------------------------------------------------- errors
+struct Error : public std::runtime_error {
+  int code;
+  Error(int c, const std::string &m) : std::runtime_error(m), code(c) {}
+};
+
+#define TT_CHECK_CUDA(call)                                                                  \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess)                                                                   \
+      throw ::tt::Error(e_ == cudaErrorMemoryAllocation ? TT_ENOMEM : TT_ECUDA,              \
+                        std::string(#call) + ": " + cudaGetErrorString(e_) + " at " +        \
+                            __FILE__ + ":" + std::to_string(__LINE__));                      \
+  } while (0)
+
+#define TT_REQUIRE(cond, msg)                                   \
+  do {                                                          \
+    if (!(cond)) throw ::tt::Error(TT_EINVAL, std::string(msg)); \
+  } while (0)
+
+struct Ctx;
+
+// ----------------------------------------------------------------- device buffer
+// Owning device allocation from the stream-ordered pool of the context stream.
+class DBuf {
+ public:
+  DBuf() = default;
+  DBuf(Ctx *c, size_t n) { alloc(c, n); }
+  ~DBuf() { release(); }
+  DBuf(const DBuf &) = delete;
+  DBuf &operator=(const DBuf &) = delete;
+  DBuf(DBuf &&o) noexcept { swap(o); }
+  DBuf &operator=(DBuf &&o) noexcept {
+    if (this != &o) {
+      release();
+      swap(o);
+    }
+    return *this;
+  }
+  void alloc(Ctx *c, size_t n);
+  // grow (contents not kept) so that at least n doubles fit
+  void ensure(Ctx *c, size_t n) {
+    if (n > cap_) alloc(c, n);
+  }
+  void release();
+  double *p() const { return p_; }
+  size_t size() const { return n_; }
+  void set_size(size_t n) { n_ = n; }
+  void swap(DBuf &o) noexcept {
+    std::swap(ctx_, o.ctx_);
+    std::swap(p_, o.p_);
+    std::swap(n_, o.n_);
+    std::swap(cap_, o.cap_);
+  }
+
+ private:
+  Ctx *ctx_ = nullptr;
+  double *p_ = nullptr;
+  size_t n_ = 0, cap_ = 0;
+};
+
+// ----------------------------------------------------------------- context
+struct Ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  int64_t launches = 0;
+  double flops = 0.0;  // algorithmic contraction flops
+  int sm_count = 152;
+  // scratch buffers reused across calls (grown on demand)
+  DBuf ws_gemm;  // split-K partial sums
+  DBuf scratch[8];
+  double *d_scalar = nullptr;  // small device area for reductions (64 doubles)
+  double *h_pinned = nullptr;  // pinned host staging (4096 doubles)
+  void sync() { TT_CHECK_CUDA(cudaStreamSynchronize(stream)); }
+  void count(int n = 1) { launches += n; }
+};
+
+// ----------------------------------------------------------------- kernels (kernels.cu)
+// C[b] = alpha op(A[b]) op(B[b]) + beta C[b], row-major, op = transpose when t* != 0.
+void gemm(Ctx *c, bool ta, bool tb, int M, int N, int K, double alpha, const double *A, int lda,
+          long long sA, const double *B, int ldb, long long sB, double beta, double *C, int ldc,
+          long long sC, int batch = 1);
+// out = permutation of a row-major tensor: out.shape[i] = in.shape[perm[i]]
+void permute(Ctx *c, const double *in, double *out, int ndim, const int *shape, const int *perm);
+// row-major rows x cols -> cols x rows
+void transpose(Ctx *c, const double *in, double *out, int rows, int cols);
+void fill(Ctx *c, double *p, size_t n, double v);
+void copy(Ctx *c, double *dst, const double *src, size_t n);
+void scale(Ctx *c, double *p, size_t n, double a);
+void axpby(Ctx *c, size_t n, double a, const double *x, double b, double *y);  // y = a x + b y
+// 2-D strided block copy: dst[i*ldd + j] = alpha * src[i*lds + j], i < rows, j < cols
+void copy2d(Ctx *c, double *dst, int ldd, const double *src, int lds, int rows, int cols,
+            double alpha = 1.0);
+// row-major rows x cols: scale row i by s[i] (device vector)
+void scale_rows(Ctx *c, double *a, int rows, int cols, const double *s);
+// deterministic reductions; result left in device memory out[0]
+void dot_dev(Ctx *c, const double *x, const double *y, size_t n, double *out);
+double dot(Ctx *c, const double *x, const double *y, size_t n);
+double nrm2(Ctx *c, const double *x, size_t n);
+// GMRES helpers: h[j] = <V_j, w> for j < nv (V rows of length n), and w -= V^T h
+void multi_dot(Ctx *c, const double *V, size_t ldv, int nv, const double *w, size_t n, double *h);
+void multi_axpy(Ctx *c, const double *V, size_t ldv, int nv, const double *h, double *w, size_t n);
+// any non-finite entry? (result to host)
+bool has_nonfinite(Ctx *c, const double *x, size_t n);
+
+// Householder QR of column-major A (m x n, lda = m), overwritten by the
+// reflectors; Q (m x k, k = min(m,n)) and R (k x n) written column-major.
+void qr_colmajor(Ctx *c, double *A, int m, int n, double *Q, double *R);
+// One-sided Jacobi SVD of a column-major square n x n matrix (destroyed):
+// U (n x n), V (n x n) column-major and S (n) sorted by decreasing value.
+void jacobi_svd(Ctx *c, double *B, int n, double *U, double *S, double *V);
+
+// Kronecker core product of the exact TT matvec:
+// Y[(a,b), i, (c,e)] = sum_j A[a,i,j,c] X[b,j,e]
+void kron_core(Ctx *c, const double *A, int R0, int m, int n, int R1, const double *X, int r0,
+               int r1, double *Y);
+// out[a, b] = sum_i w[i] G[a, i, b]  (G: r0 x n x r1), w on device
+void contract_mode(Ctx *c, const double *G, int r0, int n, int r1, const double *w, double *out);
+
+}  // namespace tt

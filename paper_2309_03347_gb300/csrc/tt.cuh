@@ -1,0 +1,88 @@
+// Tensor-train containers and algorithms (device-resident cores, host-side
+// rank bookkeeping).
+#pragma once
+#include "common.cuh"
+
+namespace tt {
+
+// TT vector (or TT matrix with mode n[k] = mo[k] * mi[k]); cores row-major
+// (r[k], n[k], r[k+1]), matrices (R[k], mo[k], mi[k], R[k+1]).
+struct TT {
+  int d = 0;
+  std::vector<int> n, r;
+  std::vector<int> mo, mi;  // matrices only (output / input mode sizes)
+  std::vector<DBuf> core;
+  bool is_matrix() const { return !mo.empty(); }
+  size_t csize(int k) const { return (size_t)r[k] * n[k] * r[k + 1]; }
+  size_t numel() const {
+    size_t s = 0;
+    for (int k = 0; k < d; ++k) s += csize(k);
+    return s;
+  }
+  int max_rank() const {
+    int m = 1;
+    for (int v : r) m = std::max(m, v);
+    return m;
+  }
+};
+
+// An operator with the permuted core layouts the contractions use.
+struct TTOp {
+  TT t;
+  std::vector<DBuf> a_ajib;  // (R0, n_in, n_out, R1)  : local matvec / left interface
+  std::vector<DBuf> a_jbai;  // (n_in, R1, R0, n_out)  : right interface
+  void prepare(Ctx *c);
+  bool prepared = false;
+};
+
+TT tt_zeros(Ctx *c, const std::vector<int> &n, const std::vector<int> &r);
+TT tt_clone(Ctx *c, const TT &x);
+TT tt_ones(Ctx *c, const std::vector<int> &n);
+TT tt_random(Ctx *c, const std::vector<int> &n, int rank, uint64_t seed);
+void tt_check(const TT &x);
+
+// SVD of a row-major m x n device matrix A (not modified).  k = min(m, n).
+// Ut: k x m (rows = left singular vectors), Vt: k x n, S: k (device and host),
+// all sorted by decreasing singular value.
+struct SVD {
+  int m = 0, n = 0, k = 0;
+  DBuf Ut, Vt, S;
+  std::vector<double> Sh;
+};
+void svd_rm(Ctx *c, const double *A, int m, int n, SVD &out);
+int trunc_rank(const std::vector<double> &s, double delta, int rmax);
+
+// QR of a row-major m x n matrix A given as its transpose At (n x m
+// row-major = A column-major, destroyed).  Q: m x k row-major, R: k x n
+// row-major, k = min(m, n).
+void qr_rm_from_t(Ctx *c, double *At, int m, int n, DBuf &Q, DBuf &R, int &k);
+
+void orth_left(Ctx *c, TT &x, int upto);   // cores 0..upto-1 left-orthogonal
+void orth_right(Ctx *c, TT &x, int downto);  // cores downto+1..d-1 right-orthogonal
+void round(Ctx *c, TT &x, double eps, int rmax);
+
+double dot(Ctx *c, const TT &x, const TT &y);
+double norm(Ctx *c, const TT &x);
+double sum(Ctx *c, const TT &x);
+void scale(Ctx *c, TT &x, double a);
+TT add(Ctx *c, double a, const TT &x, double b, const TT &y);
+TT matvec_exact(Ctx *c, const TT &A, const TT &x);
+TT transpose_op(Ctx *c, const TT &A);
+void to_dense(Ctx *c, const TT &x, double *dst, size_t len);
+TT tt_svd_dense(Ctx *c, const double *a, const std::vector<int> &modes, double eps, int rmax);
+
+// AMEn (amen.cu)
+struct SolveStats {
+  int sweeps = 0;
+  double max_dx = 0.0;
+  long long gmres_iters = 0;
+};
+void amen_solve(Ctx *c, TTOp &A, const TT &b, TT &x, double eps, int rmax, int nswp, int kick,
+                uint64_t seed, SolveStats *st);
+void amen_mv(Ctx *c, TTOp &A, const TT &x, TT &y, double eps, int rmax, int nswp, int kick,
+             uint64_t seed, SolveStats *st);
+
+// operator construction (build_op.cu)
+TT build_operator(Ctx *c, const tt_problem *p, int kind, double eps_op);
+
+}  // namespace tt
