@@ -71,6 +71,13 @@ const char *tt_version(void);
  * and interface updates). */
 int tt_ctx_counters(tt_ctx *ctx, int64_t *launches, double *contraction_flops);
 int tt_ctx_reset_counters(tt_ctx *ctx);
+/* Per-launch timing of the dense contraction kernel (the FP64 GEMM that all
+ * core contractions run on): when enabled, every launch is bracketed by CUDA
+ * events on the context stream.  tt_ctx_gemm_stats synchronises and returns
+ * the launches, their summed device time (ms) and their algorithmic flops
+ * (2 M N K per product) since profiling was enabled. */
+int tt_ctx_set_profiling(tt_ctx *ctx, int on);
+int tt_ctx_gemm_stats(tt_ctx *ctx, int64_t *launches, double *ms, double *flops);
 
 /* ---------------------------------------------------------------- TT vectors */
 

@@ -282,7 +282,10 @@ def config(idx: int, bc: str = "vacuum") -> Problem:
     """The seeded synthetic workloads.
 
     0: 8^3 points, 2 groups, S4, homogeneous (vacuum or all-reflective);
-    1: 32^3 points, 4 groups, S8, fissile box in a c = 0.9 reflector;
+    1: 32^3 points, 4 groups, S8, fissile box in a c = 0.9 reflector, side
+       2.5 cm: about 2.5 mean free paths across, the optical size of the
+       paper's 10 cm Jezebel cube (Sec. 4.2), so that cells are thin
+       (<= 0.12 mfp) as at the paper's 128-512 points per axis;
     2: 64^3 points, 8 groups, S16, three materials in boxes.
     """
     if idx == 0:
@@ -292,7 +295,7 @@ def config(idx: int, bc: str = "vacuum") -> Problem:
             p = p.with_bc((1,) * 6)
         return p
     if idx == 1:
-        p = fissile_box(l=5, G=4, order=8, seed=1001, half_width=8,
+        p = fissile_box(l=5, G=4, order=8, seed=1001, half_width=8, side=2.5,
                         name="box32_g4_s8")
         p.eps, p.rmax = 1e-7, 64
         return p

@@ -73,6 +73,8 @@ def load():
             "tt_version": ([], C.c_char_p),
             "tt_ctx_counters": ([P, C.POINTER(C.c_int64), D], C.c_int),
             "tt_ctx_reset_counters": ([P], C.c_int),
+            "tt_ctx_set_profiling": ([P, C.c_int], C.c_int),
+            "tt_ctx_gemm_stats": ([P, C.POINTER(C.c_int64), D, D], C.c_int),
             "tt_vec_create": ([P, C.c_int, I, I, D, C.c_int, C.POINTER(P)], C.c_int),
             "tt_vec_destroy": ([P], C.c_int),
             "tt_vec_shape": ([P, I, I, I], C.c_int),
@@ -160,6 +162,16 @@ class Context:
 
     def reset_counters(self):
         self.check(self.lib.tt_ctx_reset_counters(self.h))
+
+    def set_profiling(self, on: bool):
+        self.check(self.lib.tt_ctx_set_profiling(self.h, int(bool(on))))
+
+    def gemm_stats(self):
+        n = C.c_int64()
+        ms = C.c_double()
+        f = C.c_double()
+        self.check(self.lib.tt_ctx_gemm_stats(self.h, C.byref(n), C.byref(ms), C.byref(f)))
+        return int(n.value), float(ms.value), float(f.value)
 
 
 class TTVec:

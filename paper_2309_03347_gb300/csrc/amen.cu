@@ -317,7 +317,10 @@ void amen_solve(Ctx *c, TTOp &Aop, const TT &b, TT &x, double eps, int rmax, int
         local_matvec(c, PX.L[k].p(), Aop.a_ajib[k].p(), PX.R[k + 1].p(), in, r0, R1, r0, m, m, R2, r1, r1, out,
                      T1, T2);
       };
-      git += gmres(c, G, mv, rhs.p(), sol.p(), N, loc_eps);
+      {
+        PhaseTimer pt(c, "solve.gmres");
+        git += gmres(c, G, mv, rhs.p(), sol.p(), N, loc_eps);
+      }
       // relative change of the local solution
       tmp.ensure(c, N);
       copy(c, tmp.p(), sol.p(), N);
@@ -331,7 +334,10 @@ void amen_solve(Ctx *c, TTOp &Aop, const TT &b, TT &x, double eps, int rmax, int
         break;
       }
       SVD s;
-      svd_rm(c, sol.p(), r0 * m, r1, s);
+      {
+        PhaseTimer pt(c, "amen.svd");
+        svd_rm(c, sol.p(), r0 * m, r1, s);
+      }
       double sn2 = 0;
       for (double v : s.Sh) sn2 += v * v;
       const int rk = trunc_rank(s.Sh, loc_eps * std::sqrt(sn2), rmax);
@@ -356,8 +362,11 @@ void amen_solve(Ctx *c, TTOp &Aop, const TT &b, TT &x, double eps, int rmax, int
       local_matvec(c, PZ.L[k].p(), Aop.a_ajib[k].p(), PZ.R[k + 1].p(), solt.p(), rz0, R1, r0, m, m, R2, rz1, r1,
                    tmp.p(), T1, T2);
       axpby(c, (size_t)rz0 * m * rz1, -1.0, tmp.p(), 1.0, czz.p());
-      orth_core_cols(c, z, k, czz.p());
-      split_enrich(c, x, k, s, rk, crz.p(), rz1);
+      {
+        PhaseTimer pt(c, "amen.enrich_qr");
+        orth_core_cols(c, z, k, czz.p());
+        split_enrich(c, x, k, s, rk, crz.p(), rz1);
+      }
       const int nr1 = x.r[k + 1];
       left_update(c, PX.L[k].p(), x.core[k].p(), Aop.a_ajib[k].p(), x.core[k].p(), r0, R1, r0, m, m, R2, nr1, nr1,
                   PX.L[k + 1], T1, T2);
@@ -371,6 +380,7 @@ void amen_solve(Ctx *c, TTOp &Aop, const TT &b, TT &x, double eps, int rmax, int
       break;
     }
     if (swp + 1 < nswp) {
+      PhaseTimer pt(c, "amen.reorth_ifaces");
       orth_right(c, x, 0);
       orth_right(c, z, 0);
       right_all();
@@ -437,7 +447,10 @@ void amen_mv(Ctx *c, TTOp &Aop, const TT &xin, TT &y, double eps, int rmax, int 
         break;
       }
       SVD s;
-      svd_rm(c, sol.p(), r0 * m, r1, s);
+      {
+        PhaseTimer pt(c, "amen.svd");
+        svd_rm(c, sol.p(), r0 * m, r1, s);
+      }
       double sn2 = 0;
       for (double v : s.Sh) sn2 += v * v;
       const int rk = trunc_rank(s.Sh, loc_eps * std::sqrt(sn2), rmax);
@@ -459,8 +472,11 @@ void amen_mv(Ctx *c, TTOp &Aop, const TT &xin, TT &y, double eps, int rmax, int 
       tmp.ensure(c, (size_t)rz0 * m * r1);
       gemm(c, false, false, rz0, m * r1, r0, 1.0, ZY.L[k].p(), r0, 0, solt.p(), m * r1, 0, 0.0, tmp.p(), m * r1, 0);
       gemm(c, false, false, rz0 * m, rz1, r1, -1.0, tmp.p(), r1, 0, YZ.R[k + 1].p(), rz1, 0, 1.0, czz.p(), rz1, 0);
-      orth_core_cols(c, z, k, czz.p());
-      split_enrich(c, y, k, s, rk, crz.p(), rz1);
+      {
+        PhaseTimer pt(c, "amen.enrich_qr");
+        orth_core_cols(c, z, k, czz.p());
+        split_enrich(c, y, k, s, rk, crz.p(), rz1);
+      }
       const int nr1 = y.r[k + 1];
       left_update(c, PY.L[k].p(), y.core[k].p(), Aop.a_ajib[k].p(), xin.core[k].p(), r0, R1, q0, m, n, R2, nr1, q1,
                   PY.L[k + 1], T1, T2);
@@ -473,6 +489,7 @@ void amen_mv(Ctx *c, TTOp &Aop, const TT &xin, TT &y, double eps, int rmax, int 
       break;
     }
     if (swp + 1 < nswp) {
+      PhaseTimer pt(c, "amen.reorth_ifaces");
       orth_right(c, y, 0);
       orth_right(c, z, 0);
       right_all();

@@ -120,6 +120,7 @@ int tt_ctx_create(tt_ctx **out, void *stream) {
     TT_CHECK_CUDA(cudaGetDeviceProperties(&prop, ctx->c.device));
     ctx->c.sm_count = prop.multiProcessorCount;
     ctx->c.stream = (cudaStream_t)stream;
+    ctx->c.phase_timing = getenv("KEIG_PHASE_TIMES") != nullptr;
     // keep freed blocks in the stream-ordered pool
     cudaMemPool_t pool;
     TT_CHECK_CUDA(cudaDeviceGetDefaultMemPool(&pool, ctx->c.device));
@@ -144,6 +145,10 @@ int tt_ctx_destroy(tt_ctx *ctx) {
   cudaStreamSynchronize(ctx->c.stream);
   if (ctx->c.d_scalar) cudaFree(ctx->c.d_scalar);
   if (ctx->c.h_pinned) cudaFreeHost(ctx->c.h_pinned);
+  for (auto &e : ctx->c.ev_pool) {
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
+  }
   delete ctx;
   return TT_OK;
 }
@@ -162,6 +167,25 @@ int tt_ctx_reset_counters(tt_ctx *ctx) {
   ctx->c.launches = 0;
   ctx->c.flops = 0.0;
   return TT_OK;
+}
+
+int tt_ctx_set_profiling(tt_ctx *ctx, int on) {
+  return guarded(ctx, [&] {
+    ctx->c.prof_fold();
+    ctx->c.profiling = on != 0;
+    ctx->c.gemm_flops = 0.0;
+    ctx->c.gemm_launches = 0;
+    ctx->c.gemm_ms_done = 0.0;
+  });
+}
+
+int tt_ctx_gemm_stats(tt_ctx *ctx, int64_t *launches, double *ms, double *flops) {
+  return guarded(ctx, [&] {
+    ctx->c.prof_fold();
+    if (launches) *launches = ctx->c.gemm_launches;
+    if (ms) *ms = ctx->c.gemm_ms_done;
+    if (flops) *flops = ctx->c.gemm_flops;
+  });
 }
 
 // ---------------------------------------------------------------- vectors
@@ -456,9 +480,12 @@ int keig_fixed_point(tt_ctx *ctx, const tt_problem *prob, const keig_opts *opts,
     memset(out, 0, sizeof(*out));
     // operators (Sec. 3.2-3.3)
     tt::TTOp H, S, F, LHS, RHS;
-    H.t = tt::build_operator(c, prob, TT_OP_H, opts->eps_op);
-    S.t = tt::build_operator(c, prob, TT_OP_S, opts->eps_op);
-    F.t = tt::build_operator(c, prob, TT_OP_F, opts->eps_op);
+    {
+      tt::PhaseTimer pt(c, "keig.build_ops");
+      H.t = tt::build_operator(c, prob, TT_OP_H, opts->eps_op);
+      S.t = tt::build_operator(c, prob, TT_OP_S, opts->eps_op);
+      F.t = tt::build_operator(c, prob, TT_OP_F, opts->eps_op);
+    }
     // f = F^T 1, so that sum(F Psi) = <f, Psi>
     tt::TT ones = tt::tt_ones(c, F.t.mi);
     tt::TT FT = tt::transpose_op(c, F.t);
@@ -517,9 +544,18 @@ int keig_fixed_point(tt_ctx *ctx, const tt_problem *prob, const keig_opts *opts,
       }
       k_in_op = k;
       tt::SolveStats mst, sst;
-      tt::amen_mv(c, RHS, psi, B, opts->eps, opts->rmax, opts->mv_sweeps, opts->kick, 1000 + it, &mst);
+      {
+        tt::PhaseTimer pt(c, "keig.mv");
+        tt::amen_mv(c, RHS, psi, B, opts->eps, opts->rmax, opts->mv_sweeps, opts->kick, 1000 + it, &mst);
+      }
       tt::TT psi_new = tt::tt_clone(c, psi);
-      tt::amen_solve(c, LHS, B, psi_new, opts->eps, opts->rmax, opts->solve_sweeps, opts->kick, 5000 + it, &sst);
+      {
+        tt::PhaseTimer pt(c, "keig.solve");
+        tt::amen_solve(c, LHS, B, psi_new, opts->eps, opts->rmax, opts->solve_sweeps, opts->kick, 5000 + it, &sst);
+      }
+      if (c->phase_timing)
+        fprintf(stderr, "keig it %d k %.12f mv_sweeps %d mv_dx %.2e solve_sweeps %d solve_dx %.2e gmres %lld ranks B %d psi %d\n",
+                it, k, mst.sweeps, mst.max_dx, sst.sweeps, sst.max_dx, sst.gmres_iters, B.max_rank(), psi_new.max_rank());
       const double sn = tt::dot(c, f, psi_new);
       if (!std::isfinite(sn) || sn == 0.0) throw tt::Error(TT_ENONFINITE, "keig: production became zero or non-finite");
       const double kn = k * sn;
@@ -539,6 +575,10 @@ int keig_fixed_point(tt_ctx *ctx, const tt_problem *prob, const keig_opts *opts,
         conv = 1;
         break;
       }
+    }
+    if (c->phase_timing) {
+      for (auto &p : c->phase_ms) fprintf(stderr, "phase %-22s %10.1f ms\n", p.first.c_str(), p.second);
+      c->phase_ms.clear();
     }
     out->k = k;
     out->iters = std::min(it, opts->max_iter);

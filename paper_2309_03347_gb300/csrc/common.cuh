@@ -89,9 +89,38 @@ struct Ctx {
   DBuf ws_gemm;  // split-K partial sums
   DBuf scratch[8];
   double *d_scalar = nullptr;  // small device area for reductions (64 doubles)
+  // optional per-launch timing of the contraction GEMMs (CUDA events)
+  bool profiling = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
+  size_t ev_used = 0;
+  double gemm_flops = 0.0;
+  int64_t gemm_launches = 0;
+  double gemm_ms_done = 0.0;  // folded-in time of events already read
+  void prof_begin(cudaEvent_t *b, cudaEvent_t *e);
+  void prof_fold();
   double *h_pinned = nullptr;  // pinned host staging (4096 doubles)
   void sync() { TT_CHECK_CUDA(cudaStreamSynchronize(stream)); }
+  // host-side phase timers (enabled by the KEIG_PHASE_TIMES environment variable)
+  bool phase_timing = false;
+  std::vector<std::pair<std::string, double>> phase_ms;
+  void phase_add(const char *name, double ms) {
+    for (auto &p : phase_ms)
+      if (p.first == name) {
+        p.second += ms;
+        return;
+      }
+    phase_ms.push_back({name, ms});
+  }
   void count(int n = 1) { launches += n; }
+};
+
+// Scoped phase timer: synchronises the stream at both ends when enabled.
+struct PhaseTimer {
+  Ctx *c;
+  const char *name;
+  double t0 = 0;
+  PhaseTimer(Ctx *cc, const char *n);
+  ~PhaseTimer();
 };
 
 // ----------------------------------------------------------------- kernels (kernels.cu)

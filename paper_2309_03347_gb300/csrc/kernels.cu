@@ -2,6 +2,8 @@
 // with split-K, tensor permutation, reductions, Householder QR and one-sided
 // Jacobi SVD.  Every kernel bounds-checks its indices against the sizes it is
 // given; none waits on another block.
+#include <chrono>
+
 #include "common.cuh"
 
 namespace tt {
@@ -26,7 +28,49 @@ void DBuf::release() {
   n_ = cap_ = 0;
 }
 
-static inline unsigned nblk(size_t n, int t) { return (unsigned)((n + t - 1) / t); }
+static double now_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+PhaseTimer::PhaseTimer(Ctx *cc, const char *n) : c(cc), name(n) {
+  if (c->phase_timing) {
+    cudaStreamSynchronize(c->stream);
+    t0 = now_ms();
+  }
+}
+
+PhaseTimer::~PhaseTimer() {
+  if (c->phase_timing) {
+    cudaStreamSynchronize(c->stream);
+    c->phase_add(name, now_ms() - t0);
+  }
+}
+
+void Ctx::prof_begin(cudaEvent_t *b, cudaEvent_t *e) {
+  if (ev_used == ev_pool.size()) {
+    if (ev_pool.size() >= 8192) prof_fold();
+    if (ev_used == ev_pool.size()) {
+      cudaEvent_t x, y;
+      TT_CHECK_CUDA(cudaEventCreate(&x));
+      TT_CHECK_CUDA(cudaEventCreate(&y));
+      ev_pool.push_back({x, y});
+    }
+  }
+  *b = ev_pool[ev_used].first;
+  *e = ev_pool[ev_used].second;
+  ++ev_used;
+}
+
+void Ctx::prof_fold() {
+  if (!ev_used) return;
+  TT_CHECK_CUDA(cudaStreamSynchronize(stream));
+  for (size_t i = 0; i < ev_used; ++i) {
+    float ms = 0.f;
+    TT_CHECK_CUDA(cudaEventElapsedTime(&ms, ev_pool[i].first, ev_pool[i].second));
+    gemm_ms_done += ms;
+  }
+  ev_used = 0;
+}
 
 #define LAUNCH_CHECK(c)                                   \
   do {                                                    \
@@ -184,6 +228,11 @@ void gemm(Ctx *c, bool ta, bool tb, int M, int N, int K, double alpha, const dou
     ws = c->ws_gemm.p();
   }
   dim3 grid((N + GBN - 1) / GBN, (M + GBM - 1) / GBM, batch * splitk);
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  if (c->profiling) {
+    c->prof_begin(&ev0, &ev1);
+    TT_CHECK_CUDA(cudaEventRecord(ev0, c->stream));
+  }
 #define GEMM_LAUNCH(TA_, TB_)                                                                       \
   dgemm_kernel<TA_, TB_><<<grid, 256, 0, c->stream>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, \
                                                       C, ldc, sC, splitk, kchunk, ws)
@@ -198,6 +247,11 @@ void gemm(Ctx *c, bool ta, bool tb, int M, int N, int K, double alpha, const dou
     const unsigned blocks = (unsigned)std::min<long long>((tot + 255) / 256, 4LL * c->sm_count * 8);
     splitk_reduce<<<blocks, 256, 0, c->stream>>>(M, N, splitk, batch, ws, alpha, beta, C, ldc, sC);
     LAUNCH_CHECK(c);
+  }
+  if (c->profiling) {
+    TT_CHECK_CUDA(cudaEventRecord(ev1, c->stream));
+    c->gemm_flops += 2.0 * M * (double)N * K * batch;
+    c->gemm_launches += 1;
   }
 }
 
@@ -556,7 +610,6 @@ __global__ void __launch_bounds__(JAC_THREADS) jacobi_svd_kernel(double *__restr
                                                                  int use_smem) {
   extern __shared__ double smem[];
   __shared__ int s_rot;
-  __shared__ double sh[32];
   double *B = use_smem ? smem : Bg;
   const long long nn = (long long)n * n;
   if (use_smem)
@@ -645,7 +698,6 @@ __global__ void __launch_bounds__(JAC_THREADS) jacobi_svd_kernel(double *__restr
       V[(long long)r * n + i] = Vtmp[(long long)j * n + i];
     }
   }
-  (void)sh;
 }
 
 void jacobi_svd(Ctx *c, double *B, int n, double *U, double *S, double *V) {
