@@ -209,17 +209,38 @@ def test_rejects_bad_inputs(ctx):
     assert e.value.code == K.TT_EINVAL
 
 
-def _oracle_keig(p, tol=1e-11):
+def _oracle_keig(p, tol=1e-12):
     return T.OracleProblem(p).keig(tol_k=tol, max_iter=20000)
 
 
+def _keig_full_rank(ctx, p, max_iter):
+    o = K.keig_default_opts()
+    o.eps, o.rmax, o.tol_k, o.tol_psi, o.max_iter = 1e-10, 0, 1e-11, 1e-7, max_iter
+    o.solve_sweeps, o.mv_sweeps = 4, 4
+    return K.keig_fixed_point(ctx, p, o, want_phi=True)
+
+
+@pytest.mark.parametrize("case", ["homogeneous_side2", "fissile_box_side3"])
+def test_keig_matches_oracle(ctx, case):
+    # 8^3 grids at full TT rank (no truncation beyond 1e-10): the QTT fixed
+    # point must reproduce the oracle's eigenpair
+    import dataclasses
+    if case == "homogeneous_side2":
+        p = dataclasses.replace(ki.config(0), side=(2.0,) * 3)
+    else:
+        p = dataclasses.replace(ki.fissile_box(l=3, G=2, order=4, seed=1003, half_width=2), side=(3.0,) * 3)
+    ref = _oracle_keig(p)
+    res = _keig_full_rank(ctx, p, 200)
+    assert abs(res["k"] - ref["k"]) / ref["k"] < 1e-6
+    assert rel(res["phi"], ref["phi"]) < 1e-5
+
+
+@pytest.mark.slow
 def test_keig_config0_vacuum(ctx):
+    # dominance ratio 0.956: about 200 power iterations to 1e-7 in k
     p = ki.config(0)
     ref = _oracle_keig(p)
-    o = K.keig_default_opts()
-    o.eps, o.rmax, o.tol_k, o.tol_psi, o.max_iter = 1e-10, 0, 1e-11, 1e-7, 600
-    o.solve_sweeps, o.mv_sweeps = 4, 4
-    res = K.keig_fixed_point(ctx, p, o, want_phi=True)
+    res = _keig_full_rank(ctx, p, 600)
     assert abs(res["k"] - ref["k"]) / ref["k"] < 1e-6
     assert rel(res["phi"], ref["phi"]) < 1e-5
 
