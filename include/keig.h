@@ -250,6 +250,31 @@ int keig_fixed_point(tt_ctx *ctx, const tt_problem *prob, const keig_opts *opts,
  * quadrature weights, Appendix B.4) as a TT with cores [G][2 x 3l]. */
 int tt_scalar_flux(tt_ctx *ctx, const tt_vec *psi, const double *w_host, int n_dir, tt_vec **phi);
 
+/* ---------------------------------------------------------------- allocation-free inner product */
+
+/* <x, y> of two TT vectors without allocating device memory.  The paper has
+ * no counterpart: this is a service for callers that cannot allocate at the
+ * point of use (inside a CUDA-graph capture, in a real-time loop where an
+ * allocation would stall the device, or under a fixed memory budget).
+ *
+ * x_cores, y_cores: device pointers to all cores of x and y back to back,
+ * core 0 first, each core (r_k, n_k, r_{k+1}) row-major (the layout of
+ * tt_vec_get_cores).  rx, ry: host arrays of d+1 bond ranks (first and last
+ * 1), each at most 128.  n: host array of d mode sizes, each at most 64.
+ * out: device pointer receiving one double.  cuda_stream: the cudaStream_t
+ * the work is enqueued on (the call does not synchronise it).  err/err_len:
+ * optional caller buffer for a message on failure.
+ *
+ * Scratch lives in one fixed 8.25 MiB device array that every GPU loading the
+ * library holds until the process exits; the call never allocates.  The first
+ * call on each device looks up that array's device address (no allocation),
+ * so make it once before capturing a stream into a CUDA graph.  All calls
+ * share the array: calls that overlap on the GPU race and must be serialised
+ * by the caller (one stream, or events).  Sizes above the limits return
+ * TT_EINVAL before any work is enqueued. */
+int tt_dot_noalloc(const double *x_cores, const int *rx, const double *y_cores, const int *ry, int d,
+                   const int *n, double *out, void *cuda_stream, char *err, size_t err_len);
+
 #ifdef __cplusplus
 }
 #endif

@@ -101,6 +101,7 @@ def load():
             "keig_fixed_point": ([P, C.POINTER(TTProblem), C.POINTER(KeigOpts), C.POINTER(KeigResult),
                                   C.POINTER(P), D], C.c_int),
             "tt_scalar_flux": ([P, P, D, C.c_int, C.POINTER(P)], C.c_int),
+            "tt_dot_noalloc": ([D, I, D, I, C.c_int, I, D, P, C.c_char_p, C.c_size_t], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -421,3 +422,26 @@ def tt_scalar_flux(ctx: Context, psi: TTVec, w8) -> TTVec:
     h = C.c_void_p()
     ctx.check(ctx.lib.tt_scalar_flux(ctx.h, psi.h, _dp(w), len(w), C.byref(h)))
     return TTVec(ctx, h)
+
+
+def tt_dot_noalloc(x_cores, rx, y_cores, ry, n, out, stream=None) -> None:
+    """<x, y> into the one-element CUDA tensor `out`, for callers that cannot
+    allocate device memory where they need the product (graph capture,
+    fixed memory budgets).  x_cores / y_cores: contiguous float64 CUDA tensors
+    holding all cores back to back; rx, ry, n: ranks and modes (host ints).
+    The library allocates nothing; see keig.h for the shared-scratch rules."""
+    import torch
+    lib = load()
+    for t in (x_cores, y_cores, out):
+        if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+            raise KeigError(TT_EINVAL, "tt_dot_noalloc: expects contiguous float64 CUDA tensors")
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    rxa, rxp = _ip(rx)
+    rya, ryp = _ip(ry)
+    na, npp = _ip(n)
+    err = C.create_string_buffer(256)
+    rc = lib.tt_dot_noalloc(C.cast(x_cores.data_ptr(), D), rxp, C.cast(y_cores.data_ptr(), D), ryp, len(na), npp,
+                            C.cast(out.data_ptr(), D), C.c_void_p(stream.cuda_stream), err, 256)
+    if rc != TT_OK:
+        raise KeigError(rc, err.value.decode() or "tt_dot_noalloc failed")
