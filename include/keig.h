@@ -163,7 +163,11 @@ typedef enum {
 typedef enum {
   TT_FP64 = 0,        /* every contraction in FP64 */
   TT_TF32_SPLIT = 1,  /* reserved: contractions on tensor cores (not built) */
-  TT_BF16_SPLIT = 2   /* reserved: contractions on tensor cores (not built) */
+  TT_BF16_SPLIT = 2,  /* reserved: contractions on tensor cores (not built) */
+  TT_FP32_REFINED = 3 /* linear solves: Krylov iterations of each local system with FP32 contractions,
+                         wrapped in FP64 iterative refinement (FP64 residual, FP32 correction solve)
+                         until the FP64 residual meets the tolerance; products, QR/SVD, k and all
+                         interfaces stay FP64 */
 } tt_prec;
 
 /* Build H, S or F as a TT matrix with cores over the modes

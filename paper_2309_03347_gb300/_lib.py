@@ -12,6 +12,7 @@ TT_OK, TT_EINVAL, TT_ENOMEM, TT_ECUDA, TT_ENOCONV, TT_ETIMEOUT, TT_ENONFINITE = 
 TT_OP_H, TT_OP_S, TT_OP_F = 0, 1, 2
 TT_MV_EXACT, TT_MV_AMEN = 0, 1
 TT_FP64 = 0
+TT_FP32_REFINED = 3
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_FILE = os.path.join(_HERE, "_build", "libkeig_tt.so")

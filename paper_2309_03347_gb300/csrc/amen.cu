@@ -43,6 +43,19 @@ void local_matvec(Ctx *c, const double *PhiL, const double *Aajib, const double 
   c->flops += contraction_flops_local(ry1, R1, rx1, n, m, R2, rx2, ry2);
 }
 
+// FP32 version of local_matvec (operands converted once per local system)
+void local_matvec32(Ctx *c, const float *PhiL, const float *Aajib, const float *PhiR, const float *x, int ry1,
+                    int R1, int rx1, int m, int n, int R2, int ry2, int rx2, float *y, DBuf &T1, DBuf &T2) {
+  T1.ensure(c, ((size_t)ry1 * R1 * n * rx2 + 1) / 2);
+  T2.ensure(c, ((size_t)ry1 * m * R2 * rx2 + 1) / 2);
+  float *t1 = reinterpret_cast<float *>(T1.p()), *t2 = reinterpret_cast<float *>(T2.p());
+  gemm_f32(c, false, false, ry1 * R1, n * rx2, rx1, 1.f, PhiL, rx1, 0, x, n * rx2, 0, 0.f, t1, n * rx2, 0);
+  gemm_f32(c, true, false, m * R2, rx2, R1 * n, 1.f, Aajib, m * R2, 0, t1, rx2, (long long)R1 * n * rx2, 0.f, t2,
+           rx2, (long long)m * R2 * rx2, ry1);
+  gemm_f32(c, false, true, ry1 * m, ry2, R2 * rx2, 1.f, t2, R2 * rx2, 0, PhiR, R2 * rx2, 0, 0.f, y, ry2, 0);
+  c->flops32 += contraction_flops_local(ry1, R1, rx1, n, m, R2, rx2, ry2);
+}
+
 // Phi_L' (ry2, R2, rx2) from Phi_L (ry1, R1, rx1), y (ry1, m, ry2), A, x (rx1, n, rx2)
 void left_update(Ctx *c, const double *PhiL, const double *y, const double *Aajib, const double *x, int ry1,
                  int R1, int rx1, int m, int n, int R2, int ry2, int rx2, DBuf &out, DBuf &T1, DBuf &T2) {
@@ -205,6 +218,98 @@ int gmres(Ctx *c, Gmres &G, MV &&mv, const double *b, double *x, size_t N, doubl
   }
 }
 
+// FP32 GMRES for the correction equation of the iterative refinement:
+// M d = b with ||b|| = 1, d starts at zero.  Same algorithm as gmres().
+struct Gmres32 {
+  int restart = 30;
+  int maxit = 300;
+  DBuf V, hbuf, r, y;
+  std::vector<double> H, cs, sn, g;
+};
+
+template <class MV>
+int gmres32(Ctx *c, Gmres32 &G, MV &&mv, const float *b, float *x, size_t N, double tol) {
+  const int mr = G.restart;
+  G.V.ensure(c, ((size_t)(mr + 1) * N + 1) / 2);
+  G.hbuf.ensure(c, (size_t)2 * (mr + 1) + 4);
+  G.r.ensure(c, (N + 1) / 2);
+  G.y.ensure(c, (size_t)mr + 1);
+  G.H.assign((size_t)(mr + 1) * mr, 0.0);
+  G.cs.assign(mr, 0.0);
+  G.sn.assign(mr, 0.0);
+  G.g.assign(mr + 1, 0.0);
+  float *V = reinterpret_cast<float *>(G.V.p());
+  float *r = reinterpret_cast<float *>(G.r.p());
+  double *hd = G.hbuf.p();
+  double *hp = c->h_pinned;
+  int it = 0;
+  TT_CHECK_CUDA(cudaMemsetAsync(x, 0, N * sizeof(float), c->stream));
+  while (true) {
+    // r = b - M x
+    mv(x, r);
+    axpby_f(c, N, 1.f, b, -1.f, r);
+    dot_f_dev(c, r, r, N, hd);
+    TT_CHECK_CUDA(cudaMemcpyAsync(hp, hd, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    c->sync();
+    const double beta = std::sqrt(std::max(hp[0], 0.0));
+    if (!(beta > tol) || it >= G.maxit) return it;
+    axpby_f(c, N, (float)(1.0 / beta), r, 0.f, V);
+    std::fill(G.g.begin(), G.g.end(), 0.0);
+    G.g[0] = beta;
+    int jend = -1;
+    double res = beta;
+    for (int j = 0; j < mr; ++j) {
+      float *w = V + (size_t)(j + 1) * N;
+      mv(V + (size_t)j * N, w);
+      ++it;
+      multi_dot_f(c, V, N, j + 1, w, N, hd);
+      multi_axpy_f(c, V, N, j + 1, hd, w, N);
+      multi_dot_f(c, V, N, j + 1, w, N, hd + (mr + 1));
+      multi_axpy_f(c, V, N, j + 1, hd + (mr + 1), w, N);
+      dot_f_dev(c, w, w, N, hd + 2 * (mr + 1));
+      TT_CHECK_CUDA(cudaMemcpyAsync(hp, hd, sizeof(double) * (2 * (mr + 1) + 1), cudaMemcpyDeviceToHost,
+                                    c->stream));
+      c->sync();
+      const double hn = std::sqrt(std::max(hp[2 * (mr + 1)], 0.0));
+      double *Hc = &G.H[0];
+      for (int i = 0; i <= j; ++i) Hc[(size_t)i * mr + j] = hp[i] + hp[(mr + 1) + i];
+      Hc[(size_t)(j + 1) * mr + j] = hn;
+      if (!std::isfinite(hn)) throw Error(TT_ENONFINITE, "gmres32: non-finite Krylov vector");
+      for (int i = 0; i < j; ++i) {
+        const double a = Hc[(size_t)i * mr + j], bb = Hc[(size_t)(i + 1) * mr + j];
+        Hc[(size_t)i * mr + j] = G.cs[i] * a + G.sn[i] * bb;
+        Hc[(size_t)(i + 1) * mr + j] = -G.sn[i] * a + G.cs[i] * bb;
+      }
+      const double a = Hc[(size_t)j * mr + j], bb = Hc[(size_t)(j + 1) * mr + j];
+      const double den = std::hypot(a, bb);
+      G.cs[j] = den == 0.0 ? 1.0 : a / den;
+      G.sn[j] = den == 0.0 ? 0.0 : bb / den;
+      Hc[(size_t)j * mr + j] = den;
+      Hc[(size_t)(j + 1) * mr + j] = 0.0;
+      G.g[j + 1] = -G.sn[j] * G.g[j];
+      G.g[j] = G.cs[j] * G.g[j];
+      res = std::fabs(G.g[j + 1]);
+      jend = j;
+      const bool breakdown = hn <= 1e-30;
+      if (!breakdown) axpby_f(c, N, (float)(1.0 / hn), w, 0.f, w);
+      if (res <= tol || it >= G.maxit || breakdown) break;
+    }
+    const int kk = jend + 1;
+    std::vector<double> yv(kk, 0.0);
+    for (int i = kk - 1; i >= 0; --i) {
+      double s = G.g[i];
+      for (int l = i + 1; l < kk; ++l) s -= G.H[(size_t)i * mr + l] * yv[l];
+      const double dgl = G.H[(size_t)i * mr + i];
+      yv[i] = dgl != 0.0 ? s / dgl : 0.0;
+    }
+    for (int i = 0; i < kk; ++i) hp[i] = -yv[i];
+    TT_CHECK_CUDA(cudaMemcpyAsync(G.y.p(), hp, sizeof(double) * kk, cudaMemcpyHostToDevice, c->stream));
+    multi_axpy_f(c, V, N, kk, G.y.p(), x, N);  // x += V y
+    c->sync();
+    if (res <= tol || it >= G.maxit) return it;
+  }
+}
+
 struct Iface {
   std::vector<DBuf> L, R;
   void init(Ctx *c, int d) {
@@ -267,9 +372,11 @@ void orth_core_cols(Ctx *c, TT &z, int k, const double *blk) {
 }  // namespace
 
 void amen_solve(Ctx *c, TTOp &Aop, const TT &b, TT &x, double eps, int rmax, int nswp, int kick, uint64_t seed,
-                SolveStats *st) {
+                SolveStats *st, int prec) {
   TT &A = Aop.t;
   Aop.prepare(c);
+  const bool mixed = prec == TT_FP32_REFINED;
+  if (mixed) Aop.prepare32(c);
   const int d = A.d;
   TT_REQUIRE(b.d == d && x.d == d, "amen_solve: dimension mismatch");
   for (int k = 0; k < d; ++k)
@@ -299,7 +406,8 @@ void amen_solve(Ctx *c, TTOp &Aop, const TT &b, TT &x, double eps, int rmax, int
   };
   right_all();
   Gmres G;
-  DBuf rhs, sol, solt, crz, czz, tmp;
+  Gmres32 G32;
+  DBuf rhs, sol, solt, crz, czz, tmp, PL32, PR32, r32, d32, r64;
   double maxdx = 0.0;
   int swp = 0;
   long long git = 0;
@@ -317,9 +425,37 @@ void amen_solve(Ctx *c, TTOp &Aop, const TT &b, TT &x, double eps, int rmax, int
         local_matvec(c, PX.L[k].p(), Aop.a_ajib[k].p(), PX.R[k + 1].p(), in, r0, R1, r0, m, m, R2, r1, r1, out,
                      T1, T2);
       };
-      {
+      if (!mixed) {
         PhaseTimer pt(c, "solve.gmres");
         git += gmres(c, G, mv, rhs.p(), sol.p(), N, loc_eps);
+      } else {
+        // iterative refinement: FP64 residual, FP32 GMRES for the correction
+        PhaseTimer pt(c, "solve.gmres_mixed");
+        const size_t nl = (size_t)r0 * R1 * r0, nr = (size_t)r1 * R2 * r1;
+        PL32.ensure(c, (nl + 1) / 2);
+        PR32.ensure(c, (nr + 1) / 2);
+        d2f(c, PX.L[k].p(), reinterpret_cast<float *>(PL32.p()), nl);
+        d2f(c, PX.R[k + 1].p(), reinterpret_cast<float *>(PR32.p()), nr);
+        const float *A32 = reinterpret_cast<const float *>(Aop.a_ajib32[k].p());
+        auto mv32 = [&](const float *in, float *out) {
+          local_matvec32(c, reinterpret_cast<const float *>(PL32.p()), A32, reinterpret_cast<const float *>(PR32.p()),
+                         in, r0, R1, r0, m, m, R2, r1, r1, out, T1, T2);
+        };
+        r32.ensure(c, (N + 1) / 2);
+        d32.ensure(c, (N + 1) / 2);
+        r64.ensure(c, N);
+        const double nb = nrm2(c, rhs.p(), N);
+        for (int ref = 0; ref < 6 && nb > 0; ++ref) {
+          mv(sol.p(), r64.p());
+          axpby(c, N, 1.0, rhs.p(), -1.0, r64.p());
+          const double nrr = nrm2(c, r64.p(), N);
+          if (!(nrr > loc_eps * nb)) break;
+          d2f(c, r64.p(), reinterpret_cast<float *>(r32.p()), N, 1.0 / nrr);
+          const double tol_in = std::max(0.3 * loc_eps * nb / nrr, 2e-6);
+          git += gmres32(c, G32, mv32, reinterpret_cast<const float *>(r32.p()), reinterpret_cast<float *>(d32.p()),
+                         N, tol_in);
+          f2d_axpy(c, reinterpret_cast<const float *>(d32.p()), sol.p(), N, nrr);
+        }
       }
       // relative change of the local solution
       tmp.ensure(c, N);

@@ -141,6 +141,7 @@ int tt_ctx_destroy(tt_ctx *ctx) {
   if (!ctx) return TT_EINVAL;
   cudaStreamSynchronize(ctx->c.stream);
   ctx->c.ws_gemm.release();
+  ctx->c.ws_gemm32.release();
   for (auto &s : ctx->c.scratch) s.release();
   cudaStreamSynchronize(ctx->c.stream);
   if (ctx->c.d_scalar) cudaFree(ctx->c.d_scalar);
@@ -396,12 +397,12 @@ int tt_solve_local(tt_ctx *ctx, const tt_op *A, const tt_vec *b, tt_vec *x, doub
   int conv = 1;
   int rc = guarded(ctx, [&] {
     TT_REQUIRE(A && b && x, "null argument");
-    TT_REQUIRE(prec == TT_FP64, "tt_solve_local: only TT_FP64 is built");
+    TT_REQUIRE(prec == TT_FP64 || prec == TT_FP32_REFINED, "tt_solve_local: prec must be TT_FP64 or TT_FP32_REFINED");
     TT_REQUIRE(eps > 0 && eps < 1, "tt_solve_local: eps in (0, 1)");
     TT_REQUIRE(max_sweeps >= 1 && kick >= 0, "tt_solve_local: bad sweeps/kick");
     tt_op *Am = const_cast<tt_op *>(A);
     tt::SolveStats st;
-    tt::amen_solve(&ctx->c, Am->op, b->t, x->t, eps, rmax, max_sweeps, kick, 4242, &st);
+    tt::amen_solve(&ctx->c, Am->op, b->t, x->t, eps, rmax, max_sweeps, kick, 4242, &st, (int)prec);
     if (sweeps_done) *sweeps_done = st.sweeps;
     if (rel_change) *rel_change = st.max_dx;
     conv = st.max_dx < eps;
@@ -470,7 +471,8 @@ int keig_fixed_point(tt_ctx *ctx, const tt_problem *prob, const keig_opts *opts,
   int rc = guarded(ctx, [&] {
     TT_REQUIRE(opts && out, "null argument");
     validate_problem(prob);
-    TT_REQUIRE(opts->prec == TT_FP64, "keig_fixed_point: only TT_FP64 is built");
+    TT_REQUIRE(opts->prec == TT_FP64 || opts->prec == TT_FP32_REFINED,
+               "keig_fixed_point: prec must be TT_FP64 or TT_FP32_REFINED");
     TT_REQUIRE(opts->eps > 0 && opts->eps < 1 && opts->max_iter >= 1, "keig_fixed_point: bad eps/max_iter");
     TT_REQUIRE(opts->scheme == 0 || opts->scheme == 1, "keig_fixed_point: scheme must be 0 or 1");
     using clk = std::chrono::steady_clock;
@@ -531,16 +533,10 @@ int keig_fixed_point(tt_ctx *ctx, const tt_problem *prob, const keig_opts *opts,
         // F's first core occupies columns [rS, rS + rF) of the (1, G*G, rS + rF) first core
         const int rtot = RHS.t.r[1], rF = rtot - rS, ncol = RHS.t.n[0];
         tt::copy2d(c, RHS.t.core[0].p() + rS, rtot, RHS.t.core[0].p() + rS, rtot, ncol, rF, fac);
-        if (RHS.prepared) {
-          RHS.prepared = false;
-          RHS.a_ajib.clear();
-          RHS.a_jbai.clear();
-        }
+        RHS.invalidate();
       } else {
         tt::scale(c, RHS.t.core[0].p(), RHS.t.csize(0), fac);
-        RHS.prepared = false;
-        RHS.a_ajib.clear();
-        RHS.a_jbai.clear();
+        RHS.invalidate();
       }
       k_in_op = k;
       tt::SolveStats mst, sst;
@@ -551,7 +547,8 @@ int keig_fixed_point(tt_ctx *ctx, const tt_problem *prob, const keig_opts *opts,
       tt::TT psi_new = tt::tt_clone(c, psi);
       {
         tt::PhaseTimer pt(c, "keig.solve");
-        tt::amen_solve(c, LHS, B, psi_new, opts->eps, opts->rmax, opts->solve_sweeps, opts->kick, 5000 + it, &sst);
+        tt::amen_solve(c, LHS, B, psi_new, opts->eps, opts->rmax, opts->solve_sweeps, opts->kick, 5000 + it, &sst,
+                       (int)opts->prec);
       }
       if (c->phase_timing)
         fprintf(stderr, "keig it %d k %.12f mv_sweeps %d mv_dx %.2e solve_sweeps %d solve_dx %.2e gmres %lld ranks B %d psi %d\n",

@@ -83,10 +83,12 @@ struct Ctx {
   cudaStream_t stream = nullptr;
   std::string err;
   int64_t launches = 0;
-  double flops = 0.0;  // algorithmic contraction flops
+  double flops = 0.0;    // algorithmic contraction flops (FP64)
+  double flops32 = 0.0;  // algorithmic contraction flops run in FP32
   int sm_count = 152;
   // scratch buffers reused across calls (grown on demand)
-  DBuf ws_gemm;  // split-K partial sums
+  DBuf ws_gemm;    // split-K partial sums (FP64)
+  DBuf ws_gemm32;  // split-K partial sums (FP32, stored in a double-typed buffer)
   DBuf scratch[8];
   double *d_scalar = nullptr;  // small device area for reductions (64 doubles)
   // optional per-launch timing of the contraction GEMMs (CUDA events)
@@ -150,6 +152,16 @@ void multi_dot(Ctx *c, const double *V, size_t ldv, int nv, const double *w, siz
 void multi_axpy(Ctx *c, const double *V, size_t ldv, int nv, const double *h, double *w, size_t n);
 // any non-finite entry? (result to host)
 bool has_nonfinite(Ctx *c, const double *x, size_t n);
+
+// FP32 counterparts used by the mixed-precision local solves
+void gemm_f32(Ctx *c, bool ta, bool tb, int M, int N, int K, float alpha, const float *A, int lda, long long sA,
+              const float *B, int ldb, long long sB, float beta, float *C, int ldc, long long sC, int batch = 1);
+void d2f(Ctx *c, const double *x, float *y, size_t n, double s = 1.0);
+void f2d_axpy(Ctx *c, const float *x, double *y, size_t n, double a);
+void axpby_f(Ctx *c, size_t n, float a, const float *x, float b, float *y);
+void multi_dot_f(Ctx *c, const float *V, size_t ldv, int nv, const float *w, size_t n, double *h);
+void multi_axpy_f(Ctx *c, const float *V, size_t ldv, int nv, const double *h, float *w, size_t n);
+void dot_f_dev(Ctx *c, const float *x, const float *y, size_t n, double *out);
 
 // Householder QR of column-major A (m x n, lda = m), overwritten by the
 // reflectors; Q (m x k, k = min(m,n)) and R (k x n) written column-major.

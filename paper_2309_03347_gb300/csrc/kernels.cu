@@ -764,3 +764,233 @@ void contract_mode(Ctx *c, const double *G, int r0, int n, int r1, const double 
 }
 
 }  // namespace tt
+
+namespace tt {
+
+// ----------------------------------------------------------------- FP32 building blocks
+// Same tiling as the FP64 GEMM, FP32 operands and accumulation (the FP32 SIMT
+// rate of an SM is 64x its FP64 rate on this part).
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(256) sgemm_kernel(int M, int N, int K, float alpha, const float *__restrict__ A,
+                                                    int lda, long long sA, const float *__restrict__ B, int ldb,
+                                                    long long sB, float beta, float *__restrict__ C, int ldc,
+                                                    long long sC, int splitk, int kchunk, float *__restrict__ ws) {
+  __shared__ float As[GBK][GBM + 1];
+  __shared__ float Bs[GBK][GBN + 1];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int bz = blockIdx.z;
+  const int batch = bz / splitk, split = bz % splitk;
+  const int m0 = blockIdx.y * GBM, n0 = blockIdx.x * GBN;
+  const int kbeg = split * kchunk;
+  const int kend = min(K, kbeg + kchunk);
+  A += batch * sA;
+  B += batch * sB;
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  for (int k0 = kbeg; k0 < kend; k0 += GBK) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = tid + 256 * q;
+      int mm, kk;
+      if (TA) {
+        mm = e & 63;
+        kk = e >> 6;
+      } else {
+        kk = e & 15;
+        mm = e >> 4;
+      }
+      const int gm = m0 + mm, gk = k0 + kk;
+      float v = 0.f;
+      if (gm < M && gk < kend) v = TA ? A[(long long)gk * lda + gm] : A[(long long)gm * lda + gk];
+      As[kk][mm] = v;
+      int nn, kb;
+      if (TB) {
+        kb = e & 15;
+        nn = e >> 4;
+      } else {
+        nn = e & 63;
+        kb = e >> 6;
+      }
+      const int gn = n0 + nn, gkb = k0 + kb;
+      float w = 0.f;
+      if (gn < N && gkb < kend) w = TB ? B[(long long)gn * ldb + gkb] : B[(long long)gkb * ldb + gn];
+      Bs[kb][nn] = w;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GBK; ++kk) {
+      float a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  if (splitk == 1) {
+    float *Cb = C + batch * sC;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int gm = m0 + ty + 16 * i;
+      if (gm >= M) continue;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int gn = n0 + tx + 16 * j;
+        if (gn >= N) continue;
+        float *cp = Cb + (long long)gm * ldc + gn;
+        *cp = beta == 0.f ? alpha * acc[i][j] : alpha * acc[i][j] + beta * *cp;
+      }
+    }
+  } else {
+    float *W = ws + (long long)bz * M * N;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int gm = m0 + ty + 16 * i;
+      if (gm >= M) continue;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int gn = n0 + tx + 16 * j;
+        if (gn < N) W[(long long)gm * N + gn] = acc[i][j];
+      }
+    }
+  }
+}
+
+__global__ void splitk_reduce_f(int M, int N, int splitk, int batch, const float *__restrict__ ws, float alpha,
+                                float beta, float *__restrict__ C, int ldc, long long sC) {
+  const long long tot = (long long)batch * M * N;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(e / ((long long)M * N));
+    const long long r = e % ((long long)M * N);
+    const int m = (int)(r / N), n = (int)(r % N);
+    float s = 0.f;
+    for (int q = 0; q < splitk; ++q) s += ws[((long long)b * splitk + q) * M * N + r];
+    float *cp = C + b * sC + (long long)m * ldc + n;
+    *cp = beta == 0.f ? alpha * s : alpha * s + beta * *cp;
+  }
+}
+
+void gemm_f32(Ctx *c, bool ta, bool tb, int M, int N, int K, float alpha, const float *A, int lda, long long sA,
+              const float *B, int ldb, long long sB, float beta, float *C, int ldc, long long sC, int batch) {
+  if (M <= 0 || N <= 0 || batch <= 0 || K <= 0) return;
+  const long long tiles = (long long)((M + GBM - 1) / GBM) * ((N + GBN - 1) / GBN) * batch;
+  int splitk = 1;
+  const long long target = 2LL * c->sm_count;
+  if (tiles < target && K > 4 * GBK) {
+    splitk = (int)std::min<long long>((target + tiles - 1) / tiles, (K + 63) / 64);
+    splitk = std::max(1, std::min(splitk, 64));
+  }
+  int kchunk = (K + splitk - 1) / splitk;
+  kchunk = (kchunk + GBK - 1) / GBK * GBK;
+  splitk = (K + kchunk - 1) / kchunk;
+  TT_REQUIRE((long long)batch * splitk <= 65535, "gemm_f32: batch too large");
+  float *ws = nullptr;
+  if (splitk > 1) {
+    c->ws_gemm32.ensure(c, ((size_t)batch * splitk * M * N + 1) / 2);
+    ws = reinterpret_cast<float *>(c->ws_gemm32.p());
+  }
+  dim3 grid((N + GBN - 1) / GBN, (M + GBM - 1) / GBM, batch * splitk);
+#define SGEMM_LAUNCH(TA_, TB_)                                                                      \
+  sgemm_kernel<TA_, TB_><<<grid, 256, 0, c->stream>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, \
+                                                      C, ldc, sC, splitk, kchunk, ws)
+  if (ta && tb) SGEMM_LAUNCH(true, true);
+  else if (ta) SGEMM_LAUNCH(true, false);
+  else if (tb) SGEMM_LAUNCH(false, true);
+  else SGEMM_LAUNCH(false, false);
+#undef SGEMM_LAUNCH
+  LAUNCH_CHECK(c);
+  if (splitk > 1) {
+    const long long tot = (long long)batch * M * N;
+    const unsigned blocks = (unsigned)std::min<long long>((tot + 255) / 256, 4LL * c->sm_count * 8);
+    splitk_reduce_f<<<blocks, 256, 0, c->stream>>>(M, N, splitk, batch, ws, alpha, beta, C, ldc, sC);
+    LAUNCH_CHECK(c);
+  }
+}
+
+__global__ void d2f_kernel(const double *__restrict__ x, float *__restrict__ y, size_t n, double s) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    y[i] = (float)(s * x[i]);
+}
+__global__ void f2d_axpy_kernel(const float *__restrict__ x, double *__restrict__ y, size_t n, double a) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    y[i] += a * (double)x[i];
+}
+__global__ void axpby_f_kernel(size_t n, float a, const float *x, float b, float *y) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    y[i] = b == 0.f ? a * x[i] : a * x[i] + b * y[i];
+}
+__global__ void multi_dot_f_kernel(const float *__restrict__ V, size_t ldv, const float *__restrict__ w, size_t n,
+                                   double *__restrict__ h) {
+  __shared__ double sh[32];
+  const float *v = V + blockIdx.x * ldv;
+  double s = 0.0;
+  for (size_t i = threadIdx.x; i < n; i += blockDim.x) s = fma((double)v[i], (double)w[i], s);
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) h[blockIdx.x] = s;
+}
+__global__ void multi_axpy_f_kernel(const float *__restrict__ V, size_t ldv, int nv, const double *__restrict__ h,
+                                    float *__restrict__ w, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int j = 0; j < nv; ++j) s = fma((double)V[j * ldv + i], h[j], s);
+    w[i] = (float)((double)w[i] - s);
+  }
+}
+__global__ void dot_f_partial(const float *__restrict__ x, const float *__restrict__ y, size_t n,
+                              double *__restrict__ part) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    s = fma((double)x[i], (double)y[i], s);
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+void d2f(Ctx *c, const double *x, float *y, size_t n, double s) {
+  if (!n) return;
+  d2f_kernel<<<ew_blocks(c, n), 256, 0, c->stream>>>(x, y, n, s);
+  LAUNCH_CHECK(c);
+}
+void f2d_axpy(Ctx *c, const float *x, double *y, size_t n, double a) {
+  if (!n) return;
+  f2d_axpy_kernel<<<ew_blocks(c, n), 256, 0, c->stream>>>(x, y, n, a);
+  LAUNCH_CHECK(c);
+}
+void axpby_f(Ctx *c, size_t n, float a, const float *x, float b, float *y) {
+  if (!n) return;
+  axpby_f_kernel<<<ew_blocks(c, n), 256, 0, c->stream>>>(n, a, x, b, y);
+  LAUNCH_CHECK(c);
+}
+void multi_dot_f(Ctx *c, const float *V, size_t ldv, int nv, const float *w, size_t n, double *h) {
+  if (nv <= 0) return;
+  multi_dot_f_kernel<<<nv, 256, 0, c->stream>>>(V, ldv, w, n, h);
+  LAUNCH_CHECK(c);
+}
+void multi_axpy_f(Ctx *c, const float *V, size_t ldv, int nv, const double *h, float *w, size_t n) {
+  if (nv <= 0 || n == 0) return;
+  multi_axpy_f_kernel<<<ew_blocks(c, n), 256, 0, c->stream>>>(V, ldv, nv, h, w, n);
+  LAUNCH_CHECK(c);
+}
+void dot_f_dev(Ctx *c, const float *x, const float *y, size_t n, double *out) {
+  c->scratch[7].ensure(c, RED_BLOCKS);
+  if (n == 0) {
+    fill(c, out, 1, 0.0);
+    return;
+  }
+  const int nb = (int)std::min<size_t>(RED_BLOCKS, (n + 255) / 256);
+  dot_f_partial<<<nb, 256, 0, c->stream>>>(x, y, n, c->scratch[7].p());
+  LAUNCH_CHECK(c);
+  sum_partials<<<1, 256, 0, c->stream>>>(c->scratch[7].p(), nb, out);
+  LAUNCH_CHECK(c);
+}
+
+}  // namespace tt

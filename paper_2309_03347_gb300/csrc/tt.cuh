@@ -31,8 +31,17 @@ struct TTOp {
   TT t;
   std::vector<DBuf> a_ajib;  // (R0, n_in, n_out, R1)  : local matvec / left interface
   std::vector<DBuf> a_jbai;  // (n_in, R1, R0, n_out)  : right interface
+  std::vector<DBuf> a_ajib32;  // FP32 copy of a_ajib (mixed-precision local solves)
   void prepare(Ctx *c);
+  void prepare32(Ctx *c);
   bool prepared = false;
+  bool prepared32 = false;
+  void invalidate() {
+    prepared = prepared32 = false;
+    a_ajib.clear();
+    a_jbai.clear();
+    a_ajib32.clear();
+  }
 };
 
 TT tt_zeros(Ctx *c, const std::vector<int> &n, const std::vector<int> &r);
@@ -78,7 +87,7 @@ struct SolveStats {
   long long gmres_iters = 0;
 };
 void amen_solve(Ctx *c, TTOp &A, const TT &b, TT &x, double eps, int rmax, int nswp, int kick,
-                uint64_t seed, SolveStats *st);
+                uint64_t seed, SolveStats *st, int prec = TT_FP64);
 void amen_mv(Ctx *c, TTOp &A, const TT &x, TT &y, double eps, int rmax, int nswp, int kick,
              uint64_t seed, SolveStats *st);
 

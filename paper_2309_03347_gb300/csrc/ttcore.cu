@@ -343,6 +343,17 @@ void TTOp::prepare(Ctx *c) {
   prepared = true;
 }
 
+void TTOp::prepare32(Ctx *c) {
+  prepare(c);
+  if (prepared32) return;
+  a_ajib32.resize(t.d);
+  for (int k = 0; k < t.d; ++k) {
+    a_ajib32[k].alloc(c, (t.csize(k) + 1) / 2);
+    d2f(c, a_ajib[k].p(), reinterpret_cast<float *>(a_ajib32[k].p()), t.csize(k));
+  }
+  prepared32 = true;
+}
+
 void to_dense(Ctx *c, const TT &x, double *dst, size_t len) {
   size_t total = 1;
   for (int k = 0; k < x.d; ++k) total *= (size_t)x.n[k];

@@ -184,6 +184,19 @@ def test_solve_local_matches_sweep(ctx):
     assert rel(got, ref) < 1e-7, info
 
 
+def test_solve_local_mixed_precision_matches_sweep(ctx):
+    # FP32 Krylov iterations inside FP64 iterative refinement reach the same
+    # FP64 tolerance as the all-FP64 solve
+    p = ki.fissile_box(l=3, G=2, order=4, seed=41, half_width=2)
+    A = K.tt_build_operator(ctx, p, 0, 1e-13)
+    bc = ki.random_cores(p.tt_modes, [1] + [2] * (len(p.tt_modes) - 1) + [1], 33)
+    x = _vec(ctx, [np.ones((1, m, 1)) for m in p.tt_modes])
+    info = K.tt_solve_local(ctx, A, _vec(ctx, bc), x, eps=1e-10, rmax=0, max_sweeps=40, kick=4,
+                            prec=K.TT_FP32_REFINED)
+    ref = T.OracleProblem(p).sweep(R.full(bc).reshape(p.psi_shape)).ravel()
+    assert rel(x.dense_cuda().cpu().numpy().ravel(), ref) < 1e-7, info
+
+
 def test_solve_local_reports_noconv(ctx):
     p = ki.homogeneous(l=2, G=2, order=4, seed=1000)
     A = K.tt_build_operator(ctx, p, 0, 1e-13)
@@ -213,11 +226,21 @@ def _oracle_keig(p, tol=1e-12):
     return T.OracleProblem(p).keig(tol_k=tol, max_iter=20000)
 
 
-def _keig_full_rank(ctx, p, max_iter):
+def _keig_full_rank(ctx, p, max_iter, prec=0):
     o = K.keig_default_opts()
     o.eps, o.rmax, o.tol_k, o.tol_psi, o.max_iter = 1e-10, 0, 1e-11, 1e-7, max_iter
     o.solve_sweeps, o.mv_sweeps = 4, 4
+    o.prec = prec
     return K.keig_fixed_point(ctx, p, o, want_phi=True)
+
+
+def test_keig_mixed_precision_matches_oracle(ctx):
+    import dataclasses
+    p = dataclasses.replace(ki.config(0), side=(2.0,) * 3)
+    ref = _oracle_keig(p)
+    res = _keig_full_rank(ctx, p, 200, prec=K.TT_FP32_REFINED)
+    assert abs(res["k"] - ref["k"]) / ref["k"] < 1e-6
+    assert rel(res["phi"], ref["phi"]) < 1e-5
 
 
 @pytest.mark.parametrize("case", ["homogeneous_side2", "fissile_box_side3"])
