@@ -250,6 +250,31 @@ int keig_default_opts(keig_opts *opts);
 int keig_fixed_point(tt_ctx *ctx, const tt_problem *prob, const keig_opts *opts, keig_result *out,
                      tt_vec **psi_out, double *phi_out);
 
+/* Sensitivities of k to every cross-section entry by the adjoint method.
+ * Differentiating H Psi = (S + F/k) Psi and testing with the adjoint
+ * eigenvector Psi^dagger of the transposed problem
+ * H^T Psi^dagger = (S^T + F^T/k) Psi^dagger gives
+ *   dk/dp = -k^2 <Psi^dagger, (dH/dp - dS/dp - (dF/dp)/k) Psi> / <Psi^dagger, F Psi>.
+ * The paper has no adjoint; it follows from Eq. (OpFormkNTE).  Both fixed
+ * points run the QTT iteration of Eq. (TT_k_eff_fixed_points) (the adjoint
+ * one on the transposed TT operators, cores with i_k and j_k swapped).  H, S
+ * and F are linear in the tables and the group matrix enters only through the
+ * first TT core, so per material one open contraction gives the G x G matrix
+ * W[g][g'] = <Psi^dagger, (e_g e_g'^T (x) B) Psi> for the collision and the
+ * source structure B, from which all derivatives follow.
+ * Outputs (host arrays, caller-owned): dk_dsig_t [n_mat][G],
+ * dk_dsig_s [n_mat][G_to][G_from], dk_dnu_sig_f [n_mat][G], dk_dchi [n_mat][G].
+ * TT_ENOCONV if either fixed point reached max_iter (outputs still written). */
+typedef struct {
+  double k;                  /* eigenvalue of the forward fixed point */
+  double k_adjoint;          /* eigenvalue of the adjoint fixed point */
+  int iters, iters_adjoint;  /* outer iterations of each */
+  double adjoint_production; /* <Psi^dagger, F Psi> with sum(F Psi) = sum(F^T Psi^dagger) = 1 */
+  double wall_ms;
+} keig_sens_info;
+int keig_sensitivities(tt_ctx *ctx, const tt_problem *prob, const keig_opts *opts, double *dk_dsig_t,
+                       double *dk_dsig_s, double *dk_dnu_sig_f, double *dk_dchi, keig_sens_info *info);
+
 /* Scalar flux of a flux TT (contract the octant and direction cores with the
  * quadrature weights, Appendix B.4) as a TT with cores [G][2 x 3l]. */
 int tt_scalar_flux(tt_ctx *ctx, const tt_vec *psi, const double *w_host, int n_dir, tt_vec **phi);

@@ -446,3 +446,61 @@ def tt_dot_noalloc(x_cores, rx, y_cores, ry, n, out, stream=None) -> None:
                             C.cast(out.data_ptr(), D), C.c_void_p(stream.cuda_stream), err, 256)
     if rc != TT_OK:
         raise KeigError(rc, err.value.decode() or "tt_dot_noalloc failed")
+
+
+class KeigSensInfo(C.Structure):
+    _fields_ = [("k", C.c_double), ("k_adjoint", C.c_double), ("iters", C.c_int), ("iters_adjoint", C.c_int),
+                ("adjoint_production", C.c_double), ("wall_ms", C.c_double)]
+
+
+def keig_sensitivities(ctx: Context, prob, opts: Optional[KeigOpts] = None, allow_noconv: bool = False):
+    """dk/d(table entry) for sig_t, sig_s, nu_sig_f and chi by the adjoint
+    fixed point (keig.h); returns dict of arrays shaped like the tables plus
+    the run information."""
+    lib = load()
+    sig = getattr(lib.keig_sensitivities, "_marshalled", False)
+    if not sig:
+        lib.keig_sensitivities.argtypes = [C.c_void_p, C.POINTER(TTProblem), C.POINTER(KeigOpts), D, D, D, D,
+                                           C.POINTER(KeigSensInfo)]
+        lib.keig_sensitivities.restype = C.c_int
+        lib.keig_sensitivities._marshalled = True
+    pa = _ProblemArrays(prob)
+    o = opts if opts is not None else keig_default_opts()
+    nm, G = prob.n_mat, prob.G
+    gt, gs, gn, gc = np.zeros((nm, G)), np.zeros((nm, G, G)), np.zeros((nm, G)), np.zeros((nm, G))
+    info = KeigSensInfo()
+    rc = lib.keig_sensitivities(ctx.h, C.byref(pa.s), C.byref(o), _dp(gt), _dp(gs), _dp(gn), _dp(gc), C.byref(info))
+    if not (allow_noconv and rc == TT_ENOCONV):
+        ctx.check(rc)
+    return dict(sig_t=gt, sig_s=gs, nu_sig_f=gn, chi=gc, k=info.k, k_adjoint=info.k_adjoint, iters=info.iters,
+                iters_adjoint=info.iters_adjoint, adjoint_production=info.adjoint_production,
+                wall_ms=info.wall_ms, code=rc)
+
+
+def keig_k_function():
+    """A torch.autograd.Function computing k from the cross-section tables
+    (sig_t, sig_s, nu_sig_f, chi) of a problem template; its backward uses the
+    adjoint sensitivities computed in the forward call."""
+    import dataclasses
+
+    import torch
+
+    class KeigK(torch.autograd.Function):
+        @staticmethod
+        def forward(fctx, sig_t, sig_s, nu_sig_f, chi, problem, ctx, opts):
+            p = dataclasses.replace(problem, sig_t=sig_t.detach().cpu().double().numpy(),
+                                    sig_s=sig_s.detach().cpu().double().numpy(),
+                                    nu_sig_f=nu_sig_f.detach().cpu().double().numpy(),
+                                    chi=chi.detach().cpu().double().numpy())
+            r = keig_sensitivities(ctx, p, opts)
+            grads = [torch.from_numpy(r[f]).to(sig_t.device, sig_t.dtype)
+                     for f in ("sig_t", "sig_s", "nu_sig_f", "chi")]
+            fctx.save_for_backward(*grads)
+            return torch.tensor(r["k"], dtype=sig_t.dtype, device=sig_t.device)
+
+        @staticmethod
+        def backward(fctx, gk):
+            gt, gs, gn, gc = fctx.saved_tensors
+            return gk * gt, gk * gs, gk * gn, gk * gc, None, None, None
+
+    return KeigK

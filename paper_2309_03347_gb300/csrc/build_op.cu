@@ -105,32 +105,23 @@ struct Term {
 
 }  // namespace
 
-TT build_operator(Ctx *c, const tt_problem *p, int kind, double eps_op) {
-  const int l = p->l, n = 1 << l, G = p->G, nd = p->n_dir, nm = p->n_mat;
-  const double dx = p->side[0] / (n - 1), dy = p->side[1] / (n - 1), dz = p->side[2] / (n - 1);
-  const int d = 3 + 3 * l;
-  // ---- QTT of the distinct spatial factors
-  std::vector<std::vector<double>> facs;
-  std::vector<std::vector<DBuf>> qf;
-  std::vector<std::vector<int>> qr;
+OpFactors make_factors(Ctx *c, const tt_problem *p) {
+  OpFactors F;
+  const int l = p->l, n = 1 << l, nm = p->n_mat;
+  const double del[3] = {p->side[0] / (n - 1), p->side[1] / (n - 1), p->side[2] / (n - 1)};
   auto add_factor = [&](std::vector<double> f) {
-    facs.push_back(std::move(f));
     std::vector<int> rk;
-    qf.push_back(qtt_factor(c, facs.back(), l, rk));
-    qr.push_back(rk);
-    return (int)facs.size() - 1;
+    F.qf.push_back(qtt_factor(c, f, l, rk));
+    F.qr.push_back(rk);
+    return (int)F.qf.size() - 1;
   };
-  // index: [axis][pos] for D, Ip, IpNoBC
-  int iD[3][2], iIp[2], iIpN[2];
-  const double del[3] = {dx, dy, dz};
   for (int pos = 0; pos < 2; ++pos) {
-    iIp[pos] = add_factor(factor_Ip(n, pos, false));
-    iIpN[pos] = add_factor(factor_Ip(n, pos, true));
-    for (int a = 0; a < 3; ++a) iD[a][pos] = add_factor(factor_D(n, del[a], pos));
+    F.iIp[pos] = add_factor(factor_Ip(n, pos, false));
+    F.iIpN[pos] = add_factor(factor_Ip(n, pos, true));
+    for (int a = 0; a < 3; ++a) F.iD[a][pos] = add_factor(factor_D(n, del[a], pos));
   }
-  // ---- material masks per (octant, material) in QTT (only when heterogeneous)
-  std::vector<TT> masks;
-  std::vector<int> mask_index((size_t)8 * nm, -1);
+  // material masks per (octant, material) in QTT (only when heterogeneous)
+  F.mask_index.assign((size_t)8 * nm, -1);
   if (nm > 1) {
     const int nc = n - 1;
     std::vector<double> mv((size_t)n * n * n);
@@ -143,18 +134,25 @@ TT build_operator(Ctx *c, const tt_problem *p, int kind, double eps_op) {
           for (int j = 0; j < n; ++j)
             for (int i = 0; i < n; ++i) {
               const int mat = p->mat[((size_t)row_cell(k, pz, n) * nc + row_cell(j, py, n)) * nc + row_cell(i, px, n)];
-              const double v = (mat == m) ? 1.0 : 0.0;
-              mv[((size_t)k * n + j) * n + i] = v;
+              mv[((size_t)k * n + j) * n + i] = (mat == m) ? 1.0 : 0.0;
               cnt += (mat == m);
             }
         if (!cnt) continue;
         DBuf dmv = upload(c, mv);
-        masks.push_back(tt_svd_dense(c, dmv.p(), mode3, 1e-14, 0));
-        mask_index[(size_t)o * nm + m] = (int)masks.size() - 1;
+        F.masks.push_back(tt_svd_dense(c, dmv.p(), mode3, 1e-14, 0));
+        F.mask_index[(size_t)o * nm + m] = (int)F.masks.size() - 1;
       }
     }
   }
-  // ---- the rank-1 terms of the requested operator
+  return F;
+}
+
+TT assemble_operator(Ctx *c, const tt_problem *p, const OpFactors &F, int kind, int only_mat, double eps_op) {
+  const int l = p->l, G = p->G, nd = p->n_dir, nm = p->n_mat;
+  // derivative kinds omit the group core (the operator is linear in the group matrix)
+  const bool group_core = !(kind == KIND_COLLISION || kind == KIND_SOURCE);
+  const int h0 = group_core ? 0 : 1;  // first head factor used
+  const int d = 3 + 3 * l - h0;
   std::vector<Term> terms;
   auto eye = [](int k) {
     std::vector<double> a((size_t)k * k, 0.0);
@@ -166,27 +164,29 @@ TT build_operator(Ctx *c, const tt_problem *p, int kind, double eps_op) {
     for (int i = 0; i < k; ++i) a[(size_t)i * k + i] = v[i];
     return a;
   };
+  std::vector<double> dirm((size_t)nd * nd);
+  for (int a = 0; a < nd; ++a)
+    for (int b = 0; b < nd; ++b) dirm[(size_t)a * nd + b] = p->w[b];
   for (int o = 0; o < 8; ++o) {
     const int px = (o & 1) ? 1 : 0, py = (o & 2) ? 1 : 0, pz = (o & 4) ? 1 : 0;
     std::vector<double> E(64, 0.0), Intg(64, 0.0);
     E[o * 8 + o] = 1.0;
     for (int j = 0; j < 8; ++j) Intg[o * 8 + j] = 1.0;
     if (kind == TT_OP_H) {
-      terms.push_back({{eye(G), E, diag(p->amu, nd)}, iIp[pz], iIp[py], iD[0][px], -1});
-      terms.push_back({{eye(G), E, diag(p->aeta, nd)}, iIp[pz], iD[1][py], iIp[px], -1});
-      terms.push_back({{eye(G), E, diag(p->axi, nd)}, iD[2][pz], iIp[py], iIp[px], -1});
-      for (int m = 0; m < nm; ++m) {
-        const int mi = nm > 1 ? mask_index[(size_t)o * nm + m] : -1;
-        if (nm > 1 && mi < 0) continue;
-        terms.push_back({{diag(p->sig_t + (size_t)m * G, G), E, eye(nd)}, iIp[pz], iIp[py], iIp[px], mi});
-      }
-    } else {
-      std::vector<double> dirm((size_t)nd * nd);
-      for (int a = 0; a < nd; ++a)
-        for (int b = 0; b < nd; ++b) dirm[(size_t)a * nd + b] = p->w[b];
-      for (int m = 0; m < nm; ++m) {
-        const int mi = nm > 1 ? mask_index[(size_t)o * nm + m] : -1;
-        if (nm > 1 && mi < 0) continue;
+      terms.push_back({{eye(G), E, diag(p->amu, nd)}, F.iIp[pz], F.iIp[py], F.iD[0][px], -1});
+      terms.push_back({{eye(G), E, diag(p->aeta, nd)}, F.iIp[pz], F.iD[1][py], F.iIp[px], -1});
+      terms.push_back({{eye(G), E, diag(p->axi, nd)}, F.iD[2][pz], F.iIp[py], F.iIp[px], -1});
+    }
+    for (int m = 0; m < nm; ++m) {
+      if (only_mat >= 0 && m != only_mat) continue;
+      const int mi = nm > 1 ? F.mask_index[(size_t)o * nm + m] : -1;
+      if (nm > 1 && mi < 0) continue;
+      if (kind == TT_OP_H || kind == KIND_COLLISION) {
+        terms.push_back({{kind == TT_OP_H ? diag(p->sig_t + (size_t)m * G, G) : std::vector<double>(), E, eye(nd)},
+                         F.iIp[pz], F.iIp[py], F.iIp[px], mi});
+      } else if (kind == KIND_SOURCE) {
+        terms.push_back({{std::vector<double>(), Intg, dirm}, F.iIpN[pz], F.iIpN[py], F.iIpN[px], mi});
+      } else {
         std::vector<double> gm((size_t)G * G);
         bool nonzero = false;
         for (int a = 0; a < G; ++a)
@@ -197,16 +197,16 @@ TT build_operator(Ctx *c, const tt_problem *p, int kind, double eps_op) {
             nonzero |= v != 0.0;
           }
         if (!nonzero) continue;
-        terms.push_back({{gm, Intg, dirm}, iIpN[pz], iIpN[py], iIpN[px], mi});
+        terms.push_back({{gm, Intg, dirm}, F.iIpN[pz], F.iIpN[py], F.iIpN[px], mi});
       }
     }
   }
   // ---- assemble each term as a TT matrix and accumulate with rounding
+  const int sp0 = 3 - h0;  // index of the first spatial core
   std::vector<int> mo(d), mi(d);
-  mo[0] = mi[0] = G;
-  mo[1] = mi[1] = 8;
-  mo[2] = mi[2] = nd;
-  for (int k = 3; k < d; ++k) mo[k] = mi[k] = 2;
+  const int hsz[3] = {G, 8, nd};
+  for (int k = 0; k < sp0; ++k) mo[k] = mi[k] = hsz[k + h0];
+  for (int k = sp0; k < d; ++k) mo[k] = mi[k] = 2;
   TT acc;
   bool have = false;
   int pending = 0;
@@ -219,21 +219,21 @@ TT build_operator(Ctx *c, const tt_problem *p, int kind, double eps_op) {
     for (int k = 0; k < d; ++k) x.n[k] = mo[k] * mi[k];
     x.r.assign(d + 1, 1);
     x.core.resize(d);
-    for (int k = 0; k < 3; ++k) x.core[k] = upload(c, t.head[k]);
+    for (int k = 0; k < sp0; ++k) x.core[k] = upload(c, t.head[k + h0]);
     const int fidx[3] = {t.fz, t.fy, t.fx};
     for (int a = 0; a < 3; ++a)
       for (int b = 0; b < l; ++b) {
-        const int k = 3 + a * l + b;
-        x.r[k] = qr[fidx[a]][b];
-        x.r[k + 1] = qr[fidx[a]][b + 1];
+        const int k = sp0 + a * l + b;
+        x.r[k] = F.qr[fidx[a]][b];
+        x.r[k + 1] = F.qr[fidx[a]][b + 1];
         x.core[k].alloc(c, x.csize(k));
-        copy(c, x.core[k].p(), qf[fidx[a]][b].p(), x.csize(k));
+        copy(c, x.core[k].p(), F.qf[fidx[a]][b].p(), x.csize(k));
       }
     if (t.mask >= 0) {
       // M (Ip (x) Ip (x) Ip): core-wise product with the diagonal mask TT
-      const TT &mk = masks[t.mask];
+      const TT &mk = F.masks[t.mask];
       for (int q = 0; q < 3 * l; ++q) {
-        const int k = 3 + q;
+        const int k = sp0 + q;
         const int rc0 = mk.r[q], rc1 = mk.r[q + 1], Rs0 = x.r[k], Rs1 = x.r[k + 1];
         DBuf out(c, (size_t)rc0 * Rs0 * 4 * rc1 * Rs1);
         const long long tot = (long long)rc0 * Rs0 * 4 * rc1 * Rs1;
@@ -243,10 +243,7 @@ TT build_operator(Ctx *c, const tt_problem *p, int kind, double eps_op) {
         TT_CHECK_CUDA(cudaGetLastError());
         x.core[k] = std::move(out);
       }
-      for (int q = 0; q <= 3 * l; ++q) x.r[3 + q] = (q == 0 || q == 3 * l) ? x.r[3 + q] : mk.r[q] * x.r[3 + q];
-      // the bond between the head cores and the first spatial core keeps rank 1
-      x.r[3] = 1;
-      x.r[d] = 1;
+      for (int q = 1; q < 3 * l; ++q) x.r[sp0 + q] *= mk.r[q];
       round(c, x, 1e-14, 0);
     }
     if (!have) {
@@ -263,6 +260,11 @@ TT build_operator(Ctx *c, const tt_problem *p, int kind, double eps_op) {
   TT_REQUIRE(have, "build_operator: operator has no terms");
   round(c, acc, eps_op, 0);
   return acc;
+}
+
+TT build_operator(Ctx *c, const tt_problem *p, int kind, double eps_op) {
+  OpFactors F = make_factors(c, p);
+  return assemble_operator(c, p, F, kind, -1, eps_op);
 }
 
 }  // namespace tt

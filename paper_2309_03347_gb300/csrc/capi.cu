@@ -465,122 +465,194 @@ int keig_default_opts(keig_opts *o) {
   return TT_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+using clk = std::chrono::steady_clock;
+
+void check_opts(const keig_opts *opts) {
+  TT_REQUIRE(opts, "null options");
+  TT_REQUIRE(opts->prec == TT_FP64 || opts->prec == TT_FP32_REFINED,
+             "keig: prec must be TT_FP64 or TT_FP32_REFINED");
+  TT_REQUIRE(opts->eps > 0 && opts->eps < 1 && opts->max_iter >= 1, "keig: bad eps/max_iter");
+  TT_REQUIRE(opts->scheme == 0 || opts->scheme == 1, "keig: scheme must be 0 or 1");
+}
+
+// The operators of one problem, forward or transposed (adjoint).
+struct KeigOps {
+  tt::TTOp LHS, RHS;  // scheme 0: H and S (+) F; scheme 1: H - S and F
+  tt::TT f;           // sum(F Psi) = <f, Psi>
+  int rS = 0;         // columns of the first RHS core that belong to S (scheme 0)
+};
+
+KeigOps make_ops(tt::Ctx *c, tt::TT H, tt::TT S, tt::TT F, const keig_opts *opts) {
+  KeigOps o;
+  tt::TT ones = tt::tt_ones(c, F.mi);
+  tt::TT FT = tt::transpose_op(c, F);
+  o.f = tt::matvec_exact(c, FT, ones);
+  tt::round(c, o.f, 1e-13, 0);
+  o.rS = S.r[1];
+  if (opts->scheme == 0) {
+    o.RHS.t = tt::add(c, 1.0, S, 1.0, F);
+    o.LHS.t = std::move(H);
+  } else {
+    o.RHS.t = std::move(F);
+    o.LHS.t = tt::add(c, 1.0, H, -1.0, S);
+    tt::round(c, o.LHS.t, opts->eps_op, 0);
+  }
+  return o;
+}
+
+// Eq. (TT_k_eff_fixed_points) on prepared operators; returns convergence.
+bool run_fixed_point(tt::Ctx *c, KeigOps &ops, const keig_opts *opts, keig_result *out, tt::TT &psi,
+                     clk::time_point t0, uint64_t seed) {
+  auto ms = [&] { return std::chrono::duration<double, std::milli>(clk::now() - t0).count(); };
+  const int d = ops.LHS.t.d;
+  std::vector<int> modes = ops.LHS.t.mi;
+  psi = tt::tt_ones(c, modes);
+  if (opts->psi0_cores) {
+    size_t off = 0;
+    for (int k = 0; k < d; ++k) {
+      check_finite_host(opts->psi0_cores + off, modes[k], "psi0");
+      TT_CHECK_CUDA(cudaMemcpyAsync(psi.core[k].p(), opts->psi0_cores + off, modes[k] * sizeof(double),
+                                    cudaMemcpyHostToDevice, c->stream));
+      off += modes[k];
+    }
+  }
+  double s = tt::dot(c, ops.f, psi);
+  TT_REQUIRE(s != 0.0 && std::isfinite(s), "keig: initial guess has zero production");
+  tt::scale(c, psi, 1.0 / s);
+  double k = 1.0;
+  double k_in_op = 1.0;  // 1/k_in_op is the scale of the F block stored in RHS
+  tt::TT B = tt::tt_clone(c, psi);
+  int it = 0;
+  double dk = 1e300;
+  bool conv = false;
+  for (it = 0; it < opts->max_iter; ++it) {
+    const double fac = k_in_op / k;  // rescale the F part from 1/k_in_op to 1/k
+    if (opts->scheme == 0) {
+      // F's first core occupies columns [rS, rS + rF) of the (1, G*G, rS + rF) first core
+      const int rtot = ops.RHS.t.r[1], rF = rtot - ops.rS, ncol = ops.RHS.t.n[0];
+      tt::copy2d(c, ops.RHS.t.core[0].p() + ops.rS, rtot, ops.RHS.t.core[0].p() + ops.rS, rtot, ncol, rF, fac);
+    } else {
+      tt::scale(c, ops.RHS.t.core[0].p(), ops.RHS.t.csize(0), fac);
+    }
+    ops.RHS.invalidate();
+    k_in_op = k;
+    tt::SolveStats mst, sst;
+    {
+      tt::PhaseTimer pt(c, "keig.mv");
+      tt::amen_mv(c, ops.RHS, psi, B, opts->eps, opts->rmax, opts->mv_sweeps, opts->kick, seed + 1000 + it, &mst);
+    }
+    tt::TT psi_new = tt::tt_clone(c, psi);
+    {
+      tt::PhaseTimer pt(c, "keig.solve");
+      tt::amen_solve(c, ops.LHS, B, psi_new, opts->eps, opts->rmax, opts->solve_sweeps, opts->kick,
+                     seed + 5000 + it, &sst, (int)opts->prec);
+    }
+    if (c->phase_timing)
+      fprintf(stderr, "keig it %d k %.12f mv_sweeps %d mv_dx %.2e solve_sweeps %d solve_dx %.2e gmres %lld ranks B %d psi %d\n",
+              it, k, mst.sweeps, mst.max_dx, sst.sweeps, sst.max_dx, sst.gmres_iters, B.max_rank(), psi_new.max_rank());
+    const double sn = tt::dot(c, ops.f, psi_new);
+    if (!std::isfinite(sn) || sn == 0.0) throw tt::Error(TT_ENONFINITE, "keig: production became zero or non-finite");
+    const double kn = k * sn;
+    tt::scale(c, psi_new, 1.0 / sn);
+    // relative change of Psi: ||a - b||^2 = <a,a> + <b,b> - 2<a,b>
+    const double aa = tt::dot(c, psi_new, psi_new), bb = tt::dot(c, psi, psi), ab = tt::dot(c, psi_new, psi);
+    const double dpsi = std::sqrt(std::max(aa + bb - 2 * ab, 0.0) / std::max(aa, 1e-300));
+    dk = std::fabs(kn - k) / std::fabs(kn);
+    k = kn;
+    psi = std::move(psi_new);
+    if (it < 512) {
+      out->k_hist[it] = k;
+      out->t_hist[it] = ms();
+    }
+    if (dk < opts->tol_k && dpsi < opts->tol_psi) {
+      ++it;
+      conv = true;
+      break;
+    }
+  }
+  if (c->phase_timing) {
+    for (auto &p : c->phase_ms) fprintf(stderr, "phase %-22s %10.1f ms\n", p.first.c_str(), p.second);
+    c->phase_ms.clear();
+  }
+  out->k = k;
+  out->iters = std::min(it, opts->max_iter);
+  out->dk_last = dk;
+  out->max_rank = psi.max_rank();
+  return conv;
+}
+
+// <y, A x> by the left-interface chain over all cores
+double bilinear(tt::Ctx *c, tt::TTOp &A, const tt::TT &y, const tt::TT &x) {
+  A.prepare(c);
+  const tt::TT &a = A.t;
+  tt::DBuf phi(c, 1), nxt, T1, T2;
+  tt::fill(c, phi.p(), 1, 1.0);
+  for (int k = 0; k < a.d; ++k) {
+    tt::left_update(c, phi.p(), y.core[k].p(), A.a_ajib[k].p(), x.core[k].p(), y.r[k], a.r[k], x.r[k], a.mo[k],
+                    a.mi[k], a.r[k + 1], y.r[k + 1], x.r[k + 1], nxt, T1, T2);
+    phi.swap(nxt);
+  }
+  TT_CHECK_CUDA(cudaMemcpyAsync(c->h_pinned, phi.p(), sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  c->sync();
+  return c->h_pinned[0];
+}
+
+// W[g, g'] = <y, (e_g e_g'^T (x) B) x> for an operator B over the cores after
+// the group core: the right-interface chain of (y, B, x) over cores 1..d-1,
+// then the open contraction with the first cores of y and x.
+std::vector<double> open_bilinear(tt::Ctx *c, tt::TTOp &B, const tt::TT &y, const tt::TT &x) {
+  B.prepare(c);
+  const tt::TT &b = B.t;
+  TT_REQUIRE(b.d == y.d - 1 && b.d == x.d - 1, "open_bilinear: dimension mismatch");
+  tt::DBuf phi(c, 1), nxt, T1, T2;
+  tt::fill(c, phi.p(), 1, 1.0);
+  for (int k = y.d - 1; k >= 1; --k) {
+    const int q = k - 1;  // core index in B
+    tt::right_update(c, phi.p(), y.core[k].p(), B.a_jbai[q].p(), x.core[k].p(), y.r[k], b.r[q], x.r[k], b.mo[q],
+                     b.mi[q], b.r[q + 1], y.r[k + 1], x.r[k + 1], nxt, T1, T2);
+    phi.swap(nxt);
+  }
+  // phi: (ry1, 1, rx1);  W = y0 (G x ry1) phi x0^T (rx1 x G)
+  const int G = y.n[0], ry1 = y.r[1], rx1 = x.r[1];
+  tt::DBuf t(c, (size_t)G * rx1), W(c, (size_t)G * G);
+  tt::gemm(c, false, false, G, rx1, ry1, 1.0, y.core[0].p(), ry1, 0, phi.p(), rx1, 0, 0.0, t.p(), rx1, 0);
+  tt::gemm(c, false, true, G, G, rx1, 1.0, t.p(), rx1, 0, x.core[0].p(), rx1, 0, 0.0, W.p(), G, 0);
+  std::vector<double> w((size_t)G * G);
+  TT_CHECK_CUDA(cudaMemcpyAsync(w.data(), W.p(), w.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  c->sync();
+  return w;
+}
+
+}  // namespace
+
+extern "C" {
+
 int keig_fixed_point(tt_ctx *ctx, const tt_problem *prob, const keig_opts *opts, keig_result *out,
                      tt_vec **psi_out, double *phi_out) {
   int conv = 0;
   int rc = guarded(ctx, [&] {
-    TT_REQUIRE(opts && out, "null argument");
+    TT_REQUIRE(out, "null argument");
     validate_problem(prob);
-    TT_REQUIRE(opts->prec == TT_FP64 || opts->prec == TT_FP32_REFINED,
-               "keig_fixed_point: prec must be TT_FP64 or TT_FP32_REFINED");
-    TT_REQUIRE(opts->eps > 0 && opts->eps < 1 && opts->max_iter >= 1, "keig_fixed_point: bad eps/max_iter");
-    TT_REQUIRE(opts->scheme == 0 || opts->scheme == 1, "keig_fixed_point: scheme must be 0 or 1");
-    using clk = std::chrono::steady_clock;
+    check_opts(opts);
     const auto t0 = clk::now();
-    auto ms = [&] { return std::chrono::duration<double, std::milli>(clk::now() - t0).count(); };
     tt::Ctx *c = &ctx->c;
     memset(out, 0, sizeof(*out));
     // operators (Sec. 3.2-3.3)
-    tt::TTOp H, S, F, LHS, RHS;
+    tt::TT H, S, F;
     {
       tt::PhaseTimer pt(c, "keig.build_ops");
-      H.t = tt::build_operator(c, prob, TT_OP_H, opts->eps_op);
-      S.t = tt::build_operator(c, prob, TT_OP_S, opts->eps_op);
-      F.t = tt::build_operator(c, prob, TT_OP_F, opts->eps_op);
+      tt::OpFactors fac = tt::make_factors(c, prob);
+      H = tt::assemble_operator(c, prob, fac, TT_OP_H, -1, opts->eps_op);
+      S = tt::assemble_operator(c, prob, fac, TT_OP_S, -1, opts->eps_op);
+      F = tt::assemble_operator(c, prob, fac, TT_OP_F, -1, opts->eps_op);
     }
-    // f = F^T 1, so that sum(F Psi) = <f, Psi>
-    tt::TT ones = tt::tt_ones(c, F.t.mi);
-    tt::TT FT = tt::transpose_op(c, F.t);
-    tt::TT f = tt::matvec_exact(c, FT, ones);
-    tt::round(c, f, 1e-13, 0);
-    const int d = H.t.d;
-    // the RHS operator: scheme 0: S (+) F (first-core block of F rescaled by 1/k)
-    //                   scheme 1: F / k, LHS = H - S
-    int rS = S.t.r[1];
-    if (opts->scheme == 0) {
-      RHS.t = tt::add(c, 1.0, S.t, 1.0, F.t);
-      LHS.t = std::move(H.t);
-    } else {
-      RHS.t = tt::tt_clone(c, F.t);
-      LHS.t = tt::add(c, 1.0, H.t, -1.0, S.t);
-      tt::round(c, LHS.t, opts->eps_op, 0);
-      H.t = tt::TT();
-    }
-    // initial guess: positive rank-1 TT
-    std::vector<int> modes = LHS.t.mi;
-    tt::TT psi = tt::tt_ones(c, modes);
-    if (opts->psi0_cores) {
-      size_t off = 0;
-      for (int k = 0; k < d; ++k) {
-        check_finite_host(opts->psi0_cores + off, modes[k], "psi0");
-        TT_CHECK_CUDA(cudaMemcpyAsync(psi.core[k].p(), opts->psi0_cores + off, modes[k] * sizeof(double),
-                                      cudaMemcpyHostToDevice, c->stream));
-        off += modes[k];
-      }
-    }
-    double s = tt::dot(c, f, psi);
-    TT_REQUIRE(s != 0.0 && std::isfinite(s), "keig: initial guess has zero production");
-    tt::scale(c, psi, 1.0 / s);
-    double k = 1.0;  // scale of the F block currently stored in RHS
-    double k_in_op = 1.0;
-    tt::TT B = tt::tt_clone(c, psi);
-    int it = 0;
-    double dk = 1e300;
-    for (it = 0; it < opts->max_iter; ++it) {
-      // RHS operator for this k
-      const double fac = k_in_op / k;  // rescale the F part by (1/k) / (1/k_in_op)
-      if (opts->scheme == 0) {
-        // F's first core occupies columns [rS, rS + rF) of the (1, G*G, rS + rF) first core
-        const int rtot = RHS.t.r[1], rF = rtot - rS, ncol = RHS.t.n[0];
-        tt::copy2d(c, RHS.t.core[0].p() + rS, rtot, RHS.t.core[0].p() + rS, rtot, ncol, rF, fac);
-        RHS.invalidate();
-      } else {
-        tt::scale(c, RHS.t.core[0].p(), RHS.t.csize(0), fac);
-        RHS.invalidate();
-      }
-      k_in_op = k;
-      tt::SolveStats mst, sst;
-      {
-        tt::PhaseTimer pt(c, "keig.mv");
-        tt::amen_mv(c, RHS, psi, B, opts->eps, opts->rmax, opts->mv_sweeps, opts->kick, 1000 + it, &mst);
-      }
-      tt::TT psi_new = tt::tt_clone(c, psi);
-      {
-        tt::PhaseTimer pt(c, "keig.solve");
-        tt::amen_solve(c, LHS, B, psi_new, opts->eps, opts->rmax, opts->solve_sweeps, opts->kick, 5000 + it, &sst,
-                       (int)opts->prec);
-      }
-      if (c->phase_timing)
-        fprintf(stderr, "keig it %d k %.12f mv_sweeps %d mv_dx %.2e solve_sweeps %d solve_dx %.2e gmres %lld ranks B %d psi %d\n",
-                it, k, mst.sweeps, mst.max_dx, sst.sweeps, sst.max_dx, sst.gmres_iters, B.max_rank(), psi_new.max_rank());
-      const double sn = tt::dot(c, f, psi_new);
-      if (!std::isfinite(sn) || sn == 0.0) throw tt::Error(TT_ENONFINITE, "keig: production became zero or non-finite");
-      const double kn = k * sn;
-      tt::scale(c, psi_new, 1.0 / sn);
-      // relative change of Psi: ||a - b||^2 = <a,a> + <b,b> - 2<a,b>
-      const double aa = tt::dot(c, psi_new, psi_new), bb = tt::dot(c, psi, psi), ab = tt::dot(c, psi_new, psi);
-      const double dpsi = std::sqrt(std::max(aa + bb - 2 * ab, 0.0) / std::max(aa, 1e-300));
-      dk = std::fabs(kn - k) / std::fabs(kn);
-      k = kn;
-      psi = std::move(psi_new);
-      if (it < 512) {
-        out->k_hist[it] = k;
-        out->t_hist[it] = ms();
-      }
-      if (dk < opts->tol_k && dpsi < opts->tol_psi) {
-        ++it;
-        conv = 1;
-        break;
-      }
-    }
-    if (c->phase_timing) {
-      for (auto &p : c->phase_ms) fprintf(stderr, "phase %-22s %10.1f ms\n", p.first.c_str(), p.second);
-      c->phase_ms.clear();
-    }
-    out->k = k;
-    out->iters = std::min(it, opts->max_iter);
-    out->dk_last = dk;
-    out->max_rank = psi.max_rank();
+    KeigOps ops = make_ops(c, std::move(H), std::move(S), std::move(F), opts);
+    tt::TT psi;
+    conv = run_fixed_point(c, ops, opts, out, psi, t0, 0);
     if (phi_out) {
       // scalar flux on the vertices, dense
       const int n = 1 << prob->l;
@@ -598,10 +670,77 @@ int keig_fixed_point(tt_ctx *ctx, const tt_problem *prob, const keig_opts *opts,
     }
     if (psi_out) *psi_out = new tt_vec{c, std::move(psi)};
     c->sync();
-    out->wall_ms = ms();
+    out->wall_ms = std::chrono::duration<double, std::milli>(clk::now() - t0).count();
   });
   if (rc == TT_OK && !conv) {
     ctx->c.err = "keig_fixed_point: max_iter reached";
+    return TT_ENOCONV;
+  }
+  return rc;
+}
+
+int keig_sensitivities(tt_ctx *ctx, const tt_problem *prob, const keig_opts *opts, double *dk_dsig_t,
+                       double *dk_dsig_s, double *dk_dnu_sig_f, double *dk_dchi, keig_sens_info *info) {
+  int conv = 0;
+  int rc = guarded(ctx, [&] {
+    validate_problem(prob);
+    check_opts(opts);
+    TT_REQUIRE(dk_dsig_t && dk_dsig_s && dk_dnu_sig_f && dk_dchi, "keig_sensitivities: null output");
+    const auto t0 = clk::now();
+    tt::Ctx *c = &ctx->c;
+    const int G = prob->G, nm = prob->n_mat;
+    tt::OpFactors fac = tt::make_factors(c, prob);
+    tt::TT H = tt::assemble_operator(c, prob, fac, TT_OP_H, -1, opts->eps_op);
+    tt::TT S = tt::assemble_operator(c, prob, fac, TT_OP_S, -1, opts->eps_op);
+    tt::TT F = tt::assemble_operator(c, prob, fac, TT_OP_F, -1, opts->eps_op);
+    // forward and adjoint fixed points (the adjoint uses the transposed
+    // operators; it has the same eigenvalue)
+    keig_result fwd, adj;
+    memset(&fwd, 0, sizeof(fwd));
+    memset(&adj, 0, sizeof(adj));
+    tt::TTOp Fop;
+    Fop.t = tt::tt_clone(c, F);
+    KeigOps opsT = make_ops(c, tt::transpose_op(c, H), tt::transpose_op(c, S), tt::transpose_op(c, F), opts);
+    KeigOps ops = make_ops(c, std::move(H), std::move(S), std::move(F), opts);
+    tt::TT psi, psa;
+    const bool c1 = run_fixed_point(c, ops, opts, &fwd, psi, t0, 0);
+    const bool c2 = run_fixed_point(c, opsT, opts, &adj, psa, t0, 77);
+    conv = c1 && c2;
+    const double k = fwd.k;
+    // <Psi^dagger, F Psi>
+    const double P = bilinear(c, Fop, psa, psi);
+    TT_REQUIRE(std::isfinite(P) && P != 0.0, "keig_sensitivities: <Psi^dagger, F Psi> vanished");
+    // dk = -k^2 <Psi^dagger, (dH - dS - dF/k) Psi> / <Psi^dagger, F Psi>
+    for (int m = 0; m < nm; ++m) {
+      tt::TTOp Bc, Bs;
+      Bc.t = tt::assemble_operator(c, prob, fac, tt::KIND_COLLISION, m, opts->eps_op);
+      Bs.t = tt::assemble_operator(c, prob, fac, tt::KIND_SOURCE, m, opts->eps_op);
+      const std::vector<double> Wc = open_bilinear(c, Bc, psa, psi);
+      const std::vector<double> Ws = open_bilinear(c, Bs, psa, psi);
+      const double *chi = prob->chi + (size_t)m * G, *nsf = prob->nu_sig_f + (size_t)m * G;
+      for (int g = 0; g < G; ++g) {
+        dk_dsig_t[(size_t)m * G + g] = -k * k * Wc[(size_t)g * G + g] / P;
+        double a = 0.0, b = 0.0;
+        for (int h = 0; h < G; ++h) {
+          dk_dsig_s[((size_t)m * G + g) * G + h] = k * k * Ws[(size_t)g * G + h] / P;
+          a += chi[h] * Ws[(size_t)h * G + g];  // d/d nsf_g: sum over destination groups h
+          b += Ws[(size_t)g * G + h] * nsf[h];  // d/d chi_g: sum over source groups h
+        }
+        dk_dnu_sig_f[(size_t)m * G + g] = k * a / P;
+        dk_dchi[(size_t)m * G + g] = k * b / P;
+      }
+    }
+    if (info) {
+      info->k = fwd.k;
+      info->k_adjoint = adj.k;
+      info->iters = fwd.iters;
+      info->iters_adjoint = adj.iters;
+      info->adjoint_production = P;
+      info->wall_ms = std::chrono::duration<double, std::milli>(clk::now() - t0).count();
+    }
+  });
+  if (rc == TT_OK && !conv) {
+    ctx->c.err = "keig_sensitivities: a fixed point reached max_iter";
     return TT_ENOCONV;
   }
   return rc;

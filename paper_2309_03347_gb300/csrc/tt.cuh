@@ -90,8 +90,26 @@ void amen_solve(Ctx *c, TTOp &A, const TT &b, TT &x, double eps, int rmax, int n
                 uint64_t seed, SolveStats *st, int prec = TT_FP64);
 void amen_mv(Ctx *c, TTOp &A, const TT &x, TT &y, double eps, int rmax, int nswp, int kick,
              uint64_t seed, SolveStats *st);
+// interface updates (amen.cu); operator cores in the permuted layouts of TTOp
+void left_update(Ctx *c, const double *PhiL, const double *y, const double *Aajib, const double *x, int ry1,
+                 int R1, int rx1, int m, int n, int R2, int ry2, int rx2, DBuf &out, DBuf &T1, DBuf &T2);
+void right_update(Ctx *c, const double *PhiR, const double *y, const double *Ajbai, const double *x, int ry1,
+                  int R1, int rx1, int m, int n, int R2, int ry2, int rx2, DBuf &out, DBuf &T1, DBuf &T2);
 
 // operator construction (build_op.cu)
+// QTT factors and material masks of one problem, shared by every operator built from it
+struct OpFactors {
+  std::vector<std::vector<DBuf>> qf;
+  std::vector<std::vector<int>> qr;
+  int iD[3][2], iIp[2], iIpN[2];
+  std::vector<TT> masks;
+  std::vector<int> mask_index;
+};
+// operator kinds beyond tt_op_kind: the collision term and the S/F source
+// structure without their group core (derivatives w.r.t. the group matrices)
+enum { KIND_COLLISION = 10, KIND_SOURCE = 11 };
+OpFactors make_factors(Ctx *c, const tt_problem *p);
+TT assemble_operator(Ctx *c, const tt_problem *p, const OpFactors &F, int kind, int only_mat, double eps_op);
 TT build_operator(Ctx *c, const tt_problem *p, int kind, double eps_op);
 
 }  // namespace tt

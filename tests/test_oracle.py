@@ -229,3 +229,18 @@ def test_projected_system_reproduces_galerkin_identity():
     assert np.allclose(P.T @ P, np.eye(P.shape[1]), atol=1e-12)
     assert np.allclose(P @ x[3].ravel(), R.full(x).ravel(), atol=1e-12)
     assert np.allclose(Aloc, P.T @ A @ P)
+
+
+def test_finite_difference_gradients_match_dense_adjoint():
+    # two independent derivative computations of the oracle's k: central
+    # differences of the power iteration and the dense adjoint formula with
+    # exact operator derivatives (Kronecker assembly, linear in every entry)
+    from oracle import sensitivity as SE
+    import dataclasses
+    p = dataclasses.replace(ki.config(0), l=2, mat=np.zeros((3, 3, 3), np.uint8), side=(2.0,) * 3)
+    fd = SE.fd_gradients(p)
+    ad, k1, k2 = SE.dense_adjoint_gradients(p)
+    assert abs(k1 - k2) < 1e-10 * k1
+    scale = max(np.abs(v).max() for v in ad.values())
+    for f in SE.FIELDS:
+        assert np.abs(fd[f] - ad[f]).max() < 1e-6 * scale, f
