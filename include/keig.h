@@ -250,6 +250,17 @@ int keig_default_opts(keig_opts *opts);
 int keig_fixed_point(tt_ctx *ctx, const tt_problem *prob, const keig_opts *opts, keig_result *out,
                      tt_vec **psi_out, double *phi_out);
 
+/* Many independent problems at once (batching).  One problem's sweep is a
+ * chain of small contractions that occupies a few SMs at a time, so problems
+ * are solved side by side: n_ctx worker threads, each driving its own context
+ * (create each on its own CUDA stream), take problems from a shared counter
+ * and run keig_fixed_point on them.  probs, opts, out and status are arrays
+ * of n_prob entries (host); status[i] receives problem i's return code.
+ * Returns TT_OK when every problem returned TT_OK, else the first failing
+ * code in problem order.  Contexts must not be used elsewhere meanwhile. */
+int keig_batch(tt_ctx *const *ctxs, int n_ctx, const tt_problem *probs, const keig_opts *opts, int n_prob,
+               keig_result *out, int *status);
+
 /* Sensitivities of k to every cross-section entry by the adjoint method.
  * Differentiating H Psi = (S + F/k) Psi and testing with the adjoint
  * eigenvector Psi^dagger of the transposed problem

@@ -477,6 +477,37 @@ def keig_sensitivities(ctx: Context, prob, opts: Optional[KeigOpts] = None, allo
                 wall_ms=info.wall_ms, code=rc)
 
 
+def keig_batch(problems, opts_list, n_workers: int = 8, contexts=None):
+    """Solve independent problems side by side (keig.h: keig_batch).  One
+    context per worker, each on its own torch CUDA stream.  Returns a list of
+    result dicts (k, iters, dk, wall_ms, max_rank, code)."""
+    import torch
+    lib = load()
+    if not getattr(lib.keig_batch, "_marshalled", False):
+        lib.keig_batch.argtypes = [C.POINTER(C.c_void_p), C.c_int, C.POINTER(TTProblem), C.POINTER(KeigOpts), C.c_int,
+                                   C.POINTER(KeigResult), C.POINTER(C.c_int)]
+        lib.keig_batch.restype = C.c_int
+        lib.keig_batch._marshalled = True
+    n = len(problems)
+    if contexts is None:
+        contexts = [Context(torch.cuda.Stream()) for _ in range(max(1, min(n_workers, n)))]
+    handles = (C.c_void_p * len(contexts))(*[c.h.value for c in contexts])
+    arrays = [_ProblemArrays(p) for p in problems]
+    probs = (TTProblem * n)(*[a.s for a in arrays])
+    opts = (KeigOpts * n)(*opts_list)
+    res = (KeigResult * n)()
+    status = (C.c_int * n)()
+    lib.keig_batch(handles, len(contexts), probs, opts, n, res, status)
+    torch.cuda.synchronize()
+    out = []
+    for i in range(n):
+        r = res[i]
+        it = min(r.iters, 512)
+        out.append(dict(k=r.k, iters=r.iters, dk=r.dk_last, wall_ms=r.wall_ms, max_rank=r.max_rank,
+                        k_hist=np.array(r.k_hist[:it]), code=int(status[i])))
+    return out, contexts
+
+
 def keig_k_function():
     """A torch.autograd.Function computing k from the cross-section tables
     (sig_t, sig_s, nu_sig_f, chi) of a problem template; its backward uses the

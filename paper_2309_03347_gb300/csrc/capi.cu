@@ -1,6 +1,8 @@
 // extern "C" boundary of libkeig_tt (declared in include/keig.h) and the
 // k-eigenvalue fixed point of Eq. (TT_k_eff_fixed_points).
+#include <atomic>
 #include <chrono>
+#include <thread>
 
 #include "tt.cuh"
 
@@ -743,6 +745,30 @@ int keig_sensitivities(tt_ctx *ctx, const tt_problem *prob, const keig_opts *opt
     ctx->c.err = "keig_sensitivities: a fixed point reached max_iter";
     return TT_ENOCONV;
   }
+  return rc;
+}
+
+int keig_batch(tt_ctx *const *ctxs, int n_ctx, const tt_problem *probs, const keig_opts *opts, int n_prob,
+               keig_result *out, int *status) {
+  if (!ctxs || n_ctx < 1 || n_ctx > 1024 || !probs || !opts || !out || !status || n_prob < 0) return TT_EINVAL;
+  for (int w = 0; w < n_ctx; ++w)
+    if (!ctxs[w]) return TT_EINVAL;
+  std::atomic<int> next{0};
+  auto worker = [&](int w) {
+    cudaSetDevice(ctxs[w]->c.device);
+    for (;;) {
+      const int i = next.fetch_add(1);
+      if (i >= n_prob) break;
+      status[i] = keig_fixed_point(ctxs[w], &probs[i], &opts[i], &out[i], nullptr, nullptr);
+    }
+  };
+  std::vector<std::thread> th;
+  th.reserve(n_ctx);
+  for (int w = 0; w < n_ctx; ++w) th.emplace_back(worker, w);
+  for (auto &t : th) t.join();
+  int rc = TT_OK;
+  for (int i = 0; i < n_prob && rc == TT_OK; ++i)
+    if (status[i] != TT_OK) rc = status[i];
   return rc;
 }
 
