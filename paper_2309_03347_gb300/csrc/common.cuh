@@ -104,6 +104,7 @@ struct Ctx {
   void sync() { TT_CHECK_CUDA(cudaStreamSynchronize(stream)); }
   // host-side phase timers (enabled by the KEIG_PHASE_TIMES environment variable)
   bool phase_timing = false;
+  bool mixed_svd = true;  // KEIG_FP64_SVD disables the FP32-preconditioned Jacobi
   std::vector<std::pair<std::string, double>> phase_ms;
   void phase_add(const char *name, double ms) {
     for (auto &p : phase_ms)
@@ -169,6 +170,9 @@ void qr_colmajor(Ctx *c, double *A, int m, int n, double *Q, double *R);
 // One-sided Jacobi SVD of a column-major square n x n matrix (destroyed):
 // U (n x n), V (n x n) column-major and S (n) sorted by decreasing value.
 void jacobi_svd(Ctx *c, double *B, int n, double *U, double *S, double *V);
+// Same contract, rotations found in FP32 then polished in FP64 (svd_mixed.cu).
+bool jacobi_svd_mixed_fits(int n);
+void jacobi_svd_mixed(Ctx *c, double *B, int n, double *U, double *S, double *V);
 
 // Kronecker core product of the exact TT matvec:
 // Y[(a,b), i, (c,e)] = sum_j A[a,i,j,c] X[b,j,e]

@@ -109,6 +109,15 @@ void qr_rm_from_t(Ctx *c, double *At, int m, int n, DBuf &Q, DBuf &R, int &k) {
   transpose(c, Rc.p(), R.p(), n, k);
 }
 
+// SVD of the small square R factor: mixed-precision Jacobi above 24 columns
+// (FP32 rotations, FP64 polish), plain FP64 Jacobi below.
+static void small_svd(Ctx *c, double *R, int k, double *U, double *S, double *V) {
+  if (c->mixed_svd && k >= 24 && jacobi_svd_mixed_fits(k))
+    jacobi_svd_mixed(c, R, k, U, S, V);
+  else
+    jacobi_svd(c, R, k, U, S, V);
+}
+
 void svd_rm(Ctx *c, const double *A, int m, int n, SVD &o) {
   TT_REQUIRE(m > 0 && n > 0, "svd: empty matrix");
   o.m = m;
@@ -125,7 +134,7 @@ void svd_rm(Ctx *c, const double *A, int m, int n, SVD &o) {
     // A = Vr S (Q Ur)^T  ->  Ut = Vr^T (Vr col-major memory), Vt = Ur^T Q^T
     copy(c, work.p(), A, (size_t)m * n);
     qr_colmajor(c, work.p(), n, m, Q.p(), Rm.p());
-    jacobi_svd(c, Rm.p(), k, Ur.p(), o.S.p(), Vr.p());
+    small_svd(c, Rm.p(), k, Ur.p(), o.S.p(), Vr.p());
     copy(c, o.Ut.p(), Vr.p(), (size_t)k * k);
     // Vt (k x n row-major) = Ur^T (row-major view of Ur col-major: k x k) * Q^T (row-major view k x n)
     gemm(c, false, false, k, n, k, 1.0, Ur.p(), k, 0, Q.p(), n, 0, 0.0, o.Vt.p(), n, 0);
@@ -134,7 +143,7 @@ void svd_rm(Ctx *c, const double *A, int m, int n, SVD &o) {
     // A = (Q Ur) S Vr^T -> Ut = Ur^T Q^T, Vt = Vr^T (Vr col-major memory)
     transpose(c, A, work.p(), m, n);
     qr_colmajor(c, work.p(), m, n, Q.p(), Rm.p());
-    jacobi_svd(c, Rm.p(), k, Ur.p(), o.S.p(), Vr.p());
+    small_svd(c, Rm.p(), k, Ur.p(), o.S.p(), Vr.p());
     gemm(c, false, false, k, m, k, 1.0, Ur.p(), k, 0, Q.p(), m, 0, 0.0, o.Ut.p(), m, 0);
     copy(c, o.Vt.p(), Vr.p(), (size_t)k * k);
   }

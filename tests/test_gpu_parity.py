@@ -110,6 +110,31 @@ def test_round_rank_cap(ctx):
     assert rel(x.dense_cuda().cpu().numpy(), R.full(ref)) < 1e-10
 
 
+@pytest.mark.parametrize("eps", [0.0, 1e-9, 1e-4])
+def test_round_large_ranks(ctx, eps):
+    # bonds of 40-90 go through the FP32-preconditioned Jacobi with FP64
+    # polish; the result must still be an FP64-accurate rounding
+    modes = [4, 8, 6, 4, 4, 2]
+    ranks = [1, 4, 32, 90, 48, 8, 1]
+    c = ki.random_cores(modes, ranks, 17)
+    c = [ci * (0.8 ** np.arange(ci.shape[2]))[None, None, :] for ci in c]
+    full = R.full(c)
+    x = _vec(ctx, c)
+    K.tt_round(ctx, x, eps)
+    xr = x.dense_cuda().cpu().numpy()
+    assert rel(xr, full) <= max(eps, 1e-13) * (1 + 1e-9)
+    ref = R.tt_round(c, eps)
+    assert x.ranks == R.ranks(ref)
+    for k in range(1, len(modes)):
+        sv_gpu = np.linalg.svd(xr.reshape(int(np.prod(modes[:k])), -1), compute_uv=False)[: x.ranks[k]]
+        sv_ref = R.bond_singular_values(ref, k)[: x.ranks[k]]
+        assert np.allclose(sv_gpu, sv_ref, rtol=1e-9, atol=1e-12 * sv_ref[0])
+    # orthonormality of the non-first cores after rounding (right-orthogonal)
+    for k, core in enumerate(x.cores()[1:], start=1):
+        m = core.reshape(core.shape[0], -1)
+        assert np.abs(m @ m.T - np.eye(m.shape[0])).max() < 1e-12
+
+
 def _rand_op(modes, ranks, seed):
     rng = np.random.default_rng(seed)
     return [rng.standard_normal((ranks[k], m, m, ranks[k + 1])) for k, m in enumerate(modes)]
