@@ -38,13 +38,20 @@ def workload():
     return p
 
 
-def opts_for(K, p):
+def opts_for(K, p, prec="mixed"):
     o = K.keig_default_opts()
     o.eps, o.rmax = p.eps, p.rmax
     o.tol_k, o.tol_psi, o.max_iter = 1e-9, 1e-5, 20
     o.solve_sweeps, o.mv_sweeps, o.kick = 2, 2, 4
     o.scheme = 0
+    o.prec = K.TT_FP32_REFINED if prec == "mixed" else K.TT_FP64
     return o
+
+
+# FP32 SIMT peak of the part from its unit counts and clock: 152 SMs x 128
+# FP32 lanes x 2 flops (FMA) x the maximum SM clock.
+def fp32_simt_peak_tflops(sm_mhz=2070.0, sms=152):
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
 class Clocks:
@@ -148,6 +155,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--max-iter", type=int, default=None,
                     help="cap the outer iterations (short runs for profiler captures)")
+    ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -172,7 +180,7 @@ def main():
     import paper_2309_03347_gb300 as K
 
     ctx = K.tt_ctx_create()
-    opts = opts_for(K, p)
+    opts = opts_for(K, p, args.prec)
     if args.max_iter:
         opts.max_iter = args.max_iter
     stream = torch.cuda.current_stream()
@@ -228,6 +236,7 @@ def main():
     ctx.set_profiling(True)
     step()
     n_gemm, gemm_ms, gemm_flops = ctx.gemm_stats()
+    n32, gemm32_ms, gemm32_flops = ctx.gemm32_stats()
     ctx.set_profiling(False)
 
     if rank != 0:
@@ -236,9 +245,11 @@ def main():
     line = {
         "metric": METRIC, "value": ms_step / 1e3, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f64+f32" if args.prec == "mixed" else "f64", "data": "synthetic",
         "config": {"workload": p.name, "grid": f"{p.n}^3", "groups": p.G, "directions": p.L,
                    "side_cm": p.side[0], "rank_cap": p.rmax, "eps": p.eps, "scheme": "paper",
+                   "precision": ("FP32 Krylov contractions in FP64 iterative refinement; FP64 products, "
+                                 "rounding, k" if args.prec == "mixed" else "FP64 throughout"),
                    "l2": "flushed between steps (256 MB write)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "k": res["k"], "iters": res["iters"], "max_rank": res["max_rank"], "converged": res["code"] == 0,
@@ -246,14 +257,22 @@ def main():
         "e2e": {"value": float(np.median(e2e)), "unit": UNIT, "h2d_bytes_per_step": int(in_bytes),
                 "d2h_bytes_per_step": int(phi_bytes)},
     }
-    avg_ms = gemm_ms / max(n_gemm, 1)
-    ach = (gemm_flops / max(n_gemm, 1)) / (avg_ms * 1e-3) / 1e12 if n_gemm else 0.0
-    line["roofline"] = {"bound": "alu", "kernel": "dgemm_kernel (FP64 contraction GEMM)",
-                        "achieved": ach, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                        "frac": ach / FP64_NOMINAL_TFLOPS, "traffic": None,
-                        "peak_source": "nominal FP64 rate (recipe table); MEASURED_PEAKS.json has no FP64 entry",
-                        "launches": n_gemm, "avg_launch_us": avg_ms * 1e3,
-                        "share_of_step": gemm_ms / ms_step if ms_step else None}
+    def roof(name, n, gms, gfl, peak, source):
+        avg = gms / max(n, 1)
+        ach = (gfl / max(n, 1)) / (avg * 1e-3) / 1e12 if n else 0.0
+        return {"bound": "alu", "kernel": name, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None, "peak_source": source, "launches": n,
+                "avg_launch_us": avg * 1e3, "ms_in_step": gms, "share_of_step": gms / ms_step if ms_step else None}
+
+    sm_max = clk.summary().get("sm_max_mhz") or 2070.0
+    r64 = roof("dgemm_kernel (FP64 contraction GEMM)", n_gemm, gemm_ms, gemm_flops, FP64_NOMINAL_TFLOPS,
+               "nominal FP64 rate of the recipe table (MEASURED_PEAKS.json has no FP64 entry)")
+    r32 = roof("sgemm_kernel (FP32 contraction GEMM of the mixed-precision solves)", n32, gemm32_ms, gemm32_flops,
+               fp32_simt_peak_tflops(sm_max),
+               "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock (MEASURED_PEAKS.json has no FP32 entry)")
+    # the dominant contraction kernel of the step (by device time) carries the roofline
+    line["roofline"] = r32 if gemm32_ms > gemm_ms else r64
+    line["roofline_other_gemm"] = r64 if gemm32_ms > gemm_ms else r32
     line["contraction_tflops_step"] = cflops / max(args.steps, 1) / (ms_step * 1e-3) / 1e12
     line["clocks"] = clk.summary()
     if not args.no_cpu_baseline:

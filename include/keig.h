@@ -78,6 +78,9 @@ int tt_ctx_reset_counters(tt_ctx *ctx);
  * (2 M N K per product) since profiling was enabled. */
 int tt_ctx_set_profiling(tt_ctx *ctx, int on);
 int tt_ctx_gemm_stats(tt_ctx *ctx, int64_t *launches, double *ms, double *flops);
+/* The same for the FP32 GEMM that carries the contractions of the
+ * mixed-precision (TT_FP32_REFINED) local solves. */
+int tt_ctx_gemm32_stats(tt_ctx *ctx, int64_t *launches, double *ms, double *flops);
 
 /* ---------------------------------------------------------------- TT vectors */
 

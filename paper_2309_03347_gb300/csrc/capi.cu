@@ -177,9 +177,9 @@ int tt_ctx_set_profiling(tt_ctx *ctx, int on) {
   return guarded(ctx, [&] {
     ctx->c.prof_fold();
     ctx->c.profiling = on != 0;
-    ctx->c.gemm_flops = 0.0;
-    ctx->c.gemm_launches = 0;
-    ctx->c.gemm_ms_done = 0.0;
+    ctx->c.gemm_flops = ctx->c.gemm32_flops = 0.0;
+    ctx->c.gemm_launches = ctx->c.gemm32_launches = 0;
+    ctx->c.gemm_ms_done = ctx->c.gemm32_ms_done = 0.0;
   });
 }
 
@@ -189,6 +189,15 @@ int tt_ctx_gemm_stats(tt_ctx *ctx, int64_t *launches, double *ms, double *flops)
     if (launches) *launches = ctx->c.gemm_launches;
     if (ms) *ms = ctx->c.gemm_ms_done;
     if (flops) *flops = ctx->c.gemm_flops;
+  });
+}
+
+int tt_ctx_gemm32_stats(tt_ctx *ctx, int64_t *launches, double *ms, double *flops) {
+  return guarded(ctx, [&] {
+    ctx->c.prof_fold();
+    if (launches) *launches = ctx->c.gemm32_launches;
+    if (ms) *ms = ctx->c.gemm32_ms_done;
+    if (flops) *flops = ctx->c.gemm32_flops;
   });
 }
 

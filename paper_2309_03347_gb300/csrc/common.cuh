@@ -95,10 +95,11 @@ struct Ctx {
   bool profiling = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
   size_t ev_used = 0;
-  double gemm_flops = 0.0;
-  int64_t gemm_launches = 0;
-  double gemm_ms_done = 0.0;  // folded-in time of events already read
-  void prof_begin(cudaEvent_t *b, cudaEvent_t *e);
+  std::vector<int> ev_tag;  // 0: FP64 GEMM, 1: FP32 GEMM
+  double gemm_flops = 0.0, gemm32_flops = 0.0;
+  int64_t gemm_launches = 0, gemm32_launches = 0;
+  double gemm_ms_done = 0.0, gemm32_ms_done = 0.0;  // folded-in time of events already read
+  void prof_begin(cudaEvent_t *b, cudaEvent_t *e, int tag = 0);
   void prof_fold();
   double *h_pinned = nullptr;  // pinned host staging (4096 doubles)
   void sync() { TT_CHECK_CUDA(cudaStreamSynchronize(stream)); }

@@ -46,7 +46,7 @@ PhaseTimer::~PhaseTimer() {
   }
 }
 
-void Ctx::prof_begin(cudaEvent_t *b, cudaEvent_t *e) {
+void Ctx::prof_begin(cudaEvent_t *b, cudaEvent_t *e, int tag) {
   if (ev_used == ev_pool.size()) {
     if (ev_pool.size() >= 8192) prof_fold();
     if (ev_used == ev_pool.size()) {
@@ -54,10 +54,12 @@ void Ctx::prof_begin(cudaEvent_t *b, cudaEvent_t *e) {
       TT_CHECK_CUDA(cudaEventCreate(&x));
       TT_CHECK_CUDA(cudaEventCreate(&y));
       ev_pool.push_back({x, y});
+      ev_tag.push_back(0);
     }
   }
   *b = ev_pool[ev_used].first;
   *e = ev_pool[ev_used].second;
+  ev_tag[ev_used] = tag;
   ++ev_used;
 }
 
@@ -67,7 +69,7 @@ void Ctx::prof_fold() {
   for (size_t i = 0; i < ev_used; ++i) {
     float ms = 0.f;
     TT_CHECK_CUDA(cudaEventElapsedTime(&ms, ev_pool[i].first, ev_pool[i].second));
-    gemm_ms_done += ms;
+    (ev_tag[i] ? gemm32_ms_done : gemm_ms_done) += ms;
   }
   ev_used = 0;
 }
@@ -899,6 +901,11 @@ void gemm_f32(Ctx *c, bool ta, bool tb, int M, int N, int K, float alpha, const 
     ws = reinterpret_cast<float *>(c->ws_gemm32.p());
   }
   dim3 grid((N + GBN - 1) / GBN, (M + GBM - 1) / GBM, batch * splitk);
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  if (c->profiling) {
+    c->prof_begin(&ev0, &ev1, 1);
+    TT_CHECK_CUDA(cudaEventRecord(ev0, c->stream));
+  }
 #define SGEMM_LAUNCH(TA_, TB_)                                                                      \
   sgemm_kernel<TA_, TB_><<<grid, 256, 0, c->stream>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, \
                                                       C, ldc, sC, splitk, kchunk, ws)
@@ -913,6 +920,11 @@ void gemm_f32(Ctx *c, bool ta, bool tb, int M, int N, int K, float alpha, const 
     const unsigned blocks = (unsigned)std::min<long long>((tot + 255) / 256, 4LL * c->sm_count * 8);
     splitk_reduce_f<<<blocks, 256, 0, c->stream>>>(M, N, splitk, batch, ws, alpha, beta, C, ldc, sC);
     LAUNCH_CHECK(c);
+  }
+  if (c->profiling) {
+    TT_CHECK_CUDA(cudaEventRecord(ev1, c->stream));
+    c->gemm32_flops += 2.0 * M * (double)N * K * batch;
+    c->gemm32_launches += 1;
   }
 }
 
