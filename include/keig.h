@@ -253,6 +253,28 @@ int keig_default_opts(keig_opts *opts);
 int keig_fixed_point(tt_ctx *ctx, const tt_problem *prob, const keig_opts *opts, keig_result *out,
                      tt_vec **psi_out, double *phi_out);
 
+/* The alpha-eigenvalue problem (alpha V^{-1} + H) Psi = (S + F) Psi
+ * (Eq. (OpFormAlphaNTE)) by the paper's procedure (Eq.
+ * (alpha_eig_fixed_points)): k-eigenvalue fixed points of
+ * (H + alpha V^{-1}) Psi = (S + F/k) Psi at alpha = 0 and alpha = 0.01, then
+ * secant steps alpha' = alpha_{-1} + (1 - k_{-1})(alpha - alpha_{-1}) /
+ * (k - k_{-1}) (the printed update is dimensionally garbled; this is the
+ * secant reading) until |k - 1| < tol_k1 or max_steps (<= 64) further
+ * solves.  V^{-1} = diag(1/v) (x) (octant selector (x) I) (x) Ip^3 has the
+ * structure of the collision term, so each solve is keig_fixed_point with
+ * sigma_t + alpha / v.  prob->inv_v ([G]) is required. */
+typedef struct {
+  double alpha;          /* the alpha eigenvalue */
+  double k;              /* k at the final alpha (1 within tol_k1) */
+  int steps;             /* k-eigenvalue solves run */
+  int outer_iters;       /* their outer iterations in total */
+  double wall_ms;
+  double alpha_hist[64]; /* alpha of each solve */
+  double k_hist[64];     /* k of each solve */
+} keig_alpha_result;
+int keig_alpha(tt_ctx *ctx, const tt_problem *prob, const keig_opts *opts, double tol_k1, int max_steps,
+               keig_alpha_result *out);
+
 /* Many independent problems at once (batching).  One problem's sweep is a
  * chain of small contractions that occupies a few SMs at a time, so problems
  * are solved side by side: n_ctx worker threads, each driving its own context

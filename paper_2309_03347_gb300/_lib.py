@@ -381,7 +381,11 @@ class _ProblemArrays:
             s.side[i] = float(prob.side[i])
         s.G, s.n_mat = prob.G, prob.n_mat
         s.sig_t, s.sig_s, s.nu_sig_f, s.chi = _dp(a["sig_t"]), _dp(a["sig_s"]), _dp(a["nsf"]), _dp(a["chi"])
-        s.inv_v = None
+        if getattr(prob, "inv_v", None) is not None:
+            a["inv_v"] = np.ascontiguousarray(prob.inv_v, np.float64)
+            s.inv_v = _dp(a["inv_v"])
+        else:
+            s.inv_v = None
         s.mat = a["mat"].ctypes.data_as(C.POINTER(C.c_uint8))
         s.n_dir = q.n_per_octant
         s.amu, s.aeta, s.axi, s.w = _dp(a["amu"]), _dp(a["aeta"]), _dp(a["axi"]), _dp(a["w"])
@@ -514,6 +518,32 @@ def keig_batch(problems, opts_list, n_workers: int = 8, contexts=None):
         out.append(dict(k=r.k, iters=r.iters, dk=r.dk_last, wall_ms=r.wall_ms, max_rank=r.max_rank,
                         k_hist=np.array(r.k_hist[:it]), code=int(status[i])))
     return out, contexts
+
+
+class KeigAlphaResult(C.Structure):
+    _fields_ = [("alpha", C.c_double), ("k", C.c_double), ("steps", C.c_int), ("outer_iters", C.c_int),
+                ("wall_ms", C.c_double), ("alpha_hist", C.c_double * 64), ("k_hist", C.c_double * 64)]
+
+
+def keig_alpha(ctx: Context, prob, opts: Optional[KeigOpts] = None, tol_k1: float = 1e-9, max_steps: int = 30,
+               allow_noconv: bool = False):
+    """The alpha eigenvalue by secant steps on k(alpha) = 1 (keig.h); the
+    problem must carry inv_v."""
+    lib = load()
+    if not getattr(lib.keig_alpha, "_marshalled", False):
+        lib.keig_alpha.argtypes = [C.c_void_p, C.POINTER(TTProblem), C.POINTER(KeigOpts), C.c_double, C.c_int,
+                                   C.POINTER(KeigAlphaResult)]
+        lib.keig_alpha.restype = C.c_int
+        lib.keig_alpha._marshalled = True
+    pa = _ProblemArrays(prob)
+    o = opts if opts is not None else keig_default_opts()
+    r = KeigAlphaResult()
+    rc = lib.keig_alpha(ctx.h, C.byref(pa.s), C.byref(o), float(tol_k1), int(max_steps), C.byref(r))
+    if not (allow_noconv and rc == TT_ENOCONV):
+        ctx.check(rc)
+    n = min(r.steps, 64)
+    return dict(alpha=r.alpha, k=r.k, steps=r.steps, outer_iters=r.outer_iters, wall_ms=r.wall_ms,
+                alpha_hist=np.array(r.alpha_hist[:n]), k_hist=np.array(r.k_hist[:n]), code=rc)
 
 
 def keig_k_function():

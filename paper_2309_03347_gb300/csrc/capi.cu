@@ -758,6 +758,65 @@ int keig_sensitivities(tt_ctx *ctx, const tt_problem *prob, const keig_opts *opt
   return rc;
 }
 
+int keig_alpha(tt_ctx *ctx, const tt_problem *prob, const keig_opts *opts, double tol_k1, int max_steps,
+               keig_alpha_result *out) {
+  int conv = 0;
+  int rc = guarded(ctx, [&] {
+    validate_problem(prob);
+    check_opts(opts);
+    TT_REQUIRE(out, "keig_alpha: null result");
+    TT_REQUIRE(prob->inv_v, "keig_alpha: the problem needs inv_v");
+    check_finite_host(prob->inv_v, prob->G, "inv_v");
+    TT_REQUIRE(tol_k1 > 0 && max_steps >= 1 && max_steps <= 64, "keig_alpha: bad tolerance or step limit");
+    const auto t0 = clk::now();
+    memset(out, 0, sizeof(*out));
+    const int G = prob->G, nm = prob->n_mat;
+    std::vector<double> st((size_t)nm * G);
+    tt_problem q = *prob;
+    int n = 0;
+    // k(alpha): the k-eigenvalue of (H + alpha V^{-1}) Psi = (S + F/k) Psi.  V^{-1}
+    // has the structure of the collision term, so H + alpha V^{-1} is H with
+    // sigma_t + alpha / v.
+    auto k_of = [&](double a) {
+      for (int m = 0; m < nm; ++m)
+        for (int g = 0; g < G; ++g) st[(size_t)m * G + g] = prob->sig_t[(size_t)m * G + g] + a * prob->inv_v[g];
+      q.sig_t = st.data();
+      keig_result r;
+      const int rr = keig_fixed_point(ctx, &q, opts, &r, nullptr, nullptr);
+      if (rr != TT_OK && rr != TT_ENOCONV) throw tt::Error(rr, ctx->c.err);
+      out->outer_iters += r.iters;
+      if (n < 64) {
+        out->alpha_hist[n] = a;
+        out->k_hist[n] = r.k;
+      }
+      ++n;
+      return r.k;
+    };
+    // Eq. (alpha_eig_fixed_points): alpha^0 = 0, alpha^1 = 0.01, then the
+    // secant step on k(alpha) = 1
+    double a0 = 0.0, a1 = 0.01;
+    double k0 = k_of(a0), k1 = k_of(a1);
+    for (int s = 0; s < max_steps && std::fabs(k1 - 1.0) >= tol_k1; ++s) {
+      TT_REQUIRE(k1 != k0, "keig_alpha: k(alpha) did not change between secant points");
+      const double a2 = a0 + (1.0 - k0) * (a1 - a0) / (k1 - k0);
+      a0 = a1;
+      k0 = k1;
+      a1 = a2;
+      k1 = k_of(a1);
+    }
+    conv = std::fabs(k1 - 1.0) < tol_k1;
+    out->alpha = a1;
+    out->k = k1;
+    out->steps = n;
+    out->wall_ms = std::chrono::duration<double, std::milli>(clk::now() - t0).count();
+  });
+  if (rc == TT_OK && !conv) {
+    ctx->c.err = "keig_alpha: secant step limit reached";
+    return TT_ENOCONV;
+  }
+  return rc;
+}
+
 int keig_batch(tt_ctx *const *ctxs, int n_ctx, const tt_problem *probs, const keig_opts *opts, int n_prob,
                keig_result *out, int *status) {
   if (!ctxs || n_ctx < 1 || n_ctx > 1024 || !probs || !opts || !out || !status || n_prob < 0) return TT_EINVAL;
