@@ -100,6 +100,17 @@ class Clocks:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
+def max_over_ranks(value, dist=None, device="cpu"):
+    """The job's step time is the slowest rank's (replicas run the same
+    problem; no collective touches the data path)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def oracle_reference(p, threads=0, tol=1e-10):
     from oracle import transport as T
     t0 = time.time()
@@ -215,11 +226,7 @@ def main():
     if dist:
         dist.barrier()
     ms = [a.elapsed_time(b) for a, b in ev]
-    ms_step = float(np.median(ms))
-    if dist:
-        t = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = max_over_ranks(float(np.median(ms)), dist, "cuda")
 
     # ---- end to end: host wall time including the scalar-flux readback
     e2e = []
