@@ -44,8 +44,30 @@ def opts_for(K, p, prec="mixed"):
     o.tol_k, o.tol_psi, o.max_iter = 1e-9, 1e-5, 20
     o.solve_sweeps, o.mv_sweeps, o.kick = 2, 2, 4
     o.scheme = 0
-    o.prec = K.TT_FP32_REFINED if prec == "mixed" else K.TT_FP64
+    o.prec = {"mixed": K.TT_FP32_REFINED, "tf32": K.TT_TF32_SPLIT, "fp64": K.TT_FP64}[prec]
     return o
+
+
+PRECISION_TEXT = {
+    "mixed": "FP32 Krylov contractions (SIMT) in FP64 iterative refinement; FP64 products, rounding, k",
+    "tf32": ("FP32 Krylov contractions on tcgen05 tensor cores (TF32 three-term split, FP32 accumulation) "
+             "in FP64 iterative refinement; FP64 products, rounding, k"),
+    "fp64": "FP64 throughout",
+}
+DTYPE_TEXT = {"mixed": "f64+f32", "tf32": "f64+tf32x3", "fp64": "f64"}
+
+
+def tf32_tensor_peak_tflops():
+    """Dense TF32 tensor rate: the measured sustained bf16 cuBLAS rate of
+    MEASURED_PEAKS.json times the nominal tf32/bf16 ratio (1.1 / 2.25)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            bf16 = float(json.load(f)["bf16_tflops_sustained"])
+        src = "measured sustained bf16 x 1.1/2.25 (nominal tf32/bf16)"
+    except (OSError, KeyError, ValueError):
+        bf16 = 1700.0
+        src = "fallback sustained bf16 x 1.1/2.25 (nominal tf32/bf16)"
+    return bf16 * 1.1 / 2.25, src
 
 
 # FP32 SIMT peak of the part from its unit counts and clock: 152 SMs x 128
@@ -166,7 +188,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--max-iter", type=int, default=None,
                     help="cap the outer iterations (short runs for profiler captures)")
-    ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--prec", default="mixed", choices=["mixed", "tf32", "fp64"])
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -244,6 +266,7 @@ def main():
     step()
     n_gemm, gemm_ms, gemm_flops = ctx.gemm_stats()
     n32, gemm32_ms, gemm32_flops = ctx.gemm32_stats()
+    ntc, gemmtc_ms, gemmtc_flops = ctx.gemmtc_stats()
     ctx.set_profiling(False)
 
     if rank != 0:
@@ -252,11 +275,10 @@ def main():
     line = {
         "metric": METRIC, "value": ms_step / 1e3, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64+f32" if args.prec == "mixed" else "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": DTYPE_TEXT[args.prec], "data": "synthetic",
         "config": {"workload": p.name, "grid": f"{p.n}^3", "groups": p.G, "directions": p.L,
                    "side_cm": p.side[0], "rank_cap": p.rmax, "eps": p.eps, "scheme": "paper",
-                   "precision": ("FP32 Krylov contractions in FP64 iterative refinement; FP64 products, "
-                                 "rounding, k" if args.prec == "mixed" else "FP64 throughout"),
+                   "precision": PRECISION_TEXT[args.prec],
                    "l2": "flushed between steps (256 MB write)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "k": res["k"], "iters": res["iters"], "max_rank": res["max_rank"], "converged": res["code"] == 0,
@@ -264,10 +286,10 @@ def main():
         "e2e": {"value": float(np.median(e2e)), "unit": UNIT, "h2d_bytes_per_step": int(in_bytes),
                 "d2h_bytes_per_step": int(phi_bytes)},
     }
-    def roof(name, n, gms, gfl, peak, source):
+    def roof(name, n, gms, gfl, peak, source, bound="alu"):
         avg = gms / max(n, 1)
         ach = (gfl / max(n, 1)) / (avg * 1e-3) / 1e12 if n else 0.0
-        return {"bound": "alu", "kernel": name, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+        return {"bound": bound, "kernel": name, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                 "frac": ach / peak, "traffic": None, "peak_source": source, "launches": n,
                 "avg_launch_us": avg * 1e3, "ms_in_step": gms, "share_of_step": gms / ms_step if ms_step else None}
 
@@ -277,9 +299,13 @@ def main():
     r32 = roof("sgemm_kernel (FP32 contraction GEMM of the mixed-precision solves)", n32, gemm32_ms, gemm32_flops,
                fp32_simt_peak_tflops(sm_max),
                "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock (MEASURED_PEAKS.json has no FP32 entry)")
+    tf32_peak, tf32_src = tf32_tensor_peak_tflops()
+    rtc = roof("tc_gemm_kernel (tcgen05 TF32 three-term contraction GEMM; 3 MMA passes per product, "
+               "so frac <= 1/3)", ntc, gemmtc_ms, gemmtc_flops, tf32_peak, tf32_src, bound="tensor")
     # the dominant contraction kernel of the step (by device time) carries the roofline
-    line["roofline"] = r32 if gemm32_ms > gemm_ms else r64
-    line["roofline_other_gemm"] = r64 if gemm32_ms > gemm_ms else r32
+    roofs = sorted([(gemm_ms, r64), (gemm32_ms, r32), (gemmtc_ms, rtc)], key=lambda t: -t[0])
+    line["roofline"] = roofs[0][1]
+    line["roofline_other_gemm"] = [r for t, r in roofs[1:] if r["launches"]]
     line["contraction_tflops_step"] = cflops / max(args.steps, 1) / (ms_step * 1e-3) / 1e12
     line["clocks"] = clk.summary()
     if not args.no_cpu_baseline:

@@ -81,6 +81,9 @@ int tt_ctx_gemm_stats(tt_ctx *ctx, int64_t *launches, double *ms, double *flops)
 /* The same for the FP32 GEMM that carries the contractions of the
  * mixed-precision (TT_FP32_REFINED) local solves. */
 int tt_ctx_gemm32_stats(tt_ctx *ctx, int64_t *launches, double *ms, double *flops);
+/* The same for the tcgen05 TF32 three-term GEMM of TT_TF32_SPLIT (flops
+ * counted algorithmically, 2 M N K per product, not per MMA pass). */
+int tt_ctx_gemmtc_stats(tt_ctx *ctx, int64_t *launches, double *ms, double *flops);
 
 /* ---------------------------------------------------------------- TT vectors */
 
@@ -165,7 +168,9 @@ typedef enum {
 
 typedef enum {
   TT_FP64 = 0,        /* every contraction in FP64 */
-  TT_TF32_SPLIT = 1,  /* reserved: contractions on tensor cores (not built) */
+  TT_TF32_SPLIT = 1,  /* linear solves: as TT_FP32_REFINED, with the Krylov contractions on the tcgen05
+                         tensor cores (kind::tf32, FP32 accumulation in tensor memory) with the
+                         three-term split A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi */
   TT_BF16_SPLIT = 2,  /* reserved: contractions on tensor cores (not built) */
   TT_FP32_REFINED = 3 /* linear solves: Krylov iterations of each local system with FP32 contractions,
                          wrapped in FP64 iterative refinement (FP64 residual, FP32 correction solve)

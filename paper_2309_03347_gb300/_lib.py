@@ -13,6 +13,7 @@ TT_OP_H, TT_OP_S, TT_OP_F = 0, 1, 2
 TT_MV_EXACT, TT_MV_AMEN = 0, 1
 TT_FP64 = 0
 TT_FP32_REFINED = 3
+TT_TF32_SPLIT = 1
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_FILE = os.path.join(_HERE, "_build", "libkeig_tt.so")
@@ -77,6 +78,7 @@ def load():
             "tt_ctx_set_profiling": ([P, C.c_int], C.c_int),
             "tt_ctx_gemm_stats": ([P, C.POINTER(C.c_int64), D, D], C.c_int),
             "tt_ctx_gemm32_stats": ([P, C.POINTER(C.c_int64), D, D], C.c_int),
+            "tt_ctx_gemmtc_stats": ([P, C.POINTER(C.c_int64), D, D], C.c_int),
             "tt_vec_create": ([P, C.c_int, I, I, D, C.c_int, C.POINTER(P)], C.c_int),
             "tt_vec_destroy": ([P], C.c_int),
             "tt_vec_shape": ([P, I, I, I], C.c_int),
@@ -174,6 +176,13 @@ class Context:
         ms = C.c_double()
         f = C.c_double()
         self.check(self.lib.tt_ctx_gemm_stats(self.h, C.byref(n), C.byref(ms), C.byref(f)))
+        return int(n.value), float(ms.value), float(f.value)
+
+    def gemmtc_stats(self):
+        n = C.c_int64()
+        ms = C.c_double()
+        f = C.c_double()
+        self.check(self.lib.tt_ctx_gemmtc_stats(self.h, C.byref(n), C.byref(ms), C.byref(f)))
         return int(n.value), float(ms.value), float(f.value)
 
     def gemm32_stats(self):

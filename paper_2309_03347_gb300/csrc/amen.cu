@@ -43,16 +43,19 @@ void local_matvec(Ctx *c, const double *PhiL, const double *Aajib, const double 
   c->flops += contraction_flops_local(ry1, R1, rx1, n, m, R2, rx2, ry2);
 }
 
-// FP32 version of local_matvec (operands converted once per local system)
+// FP32 version of local_matvec (operands converted once per local system);
+// tc selects the tcgen05 TF32 three-term GEMM instead of the FP32 SIMT GEMM
 void local_matvec32(Ctx *c, const float *PhiL, const float *Aajib, const float *PhiR, const float *x, int ry1,
-                    int R1, int rx1, int m, int n, int R2, int ry2, int rx2, float *y, DBuf &T1, DBuf &T2) {
+                    int R1, int rx1, int m, int n, int R2, int ry2, int rx2, float *y, DBuf &T1, DBuf &T2,
+                    bool tc = false) {
   T1.ensure(c, ((size_t)ry1 * R1 * n * rx2 + 1) / 2);
   T2.ensure(c, ((size_t)ry1 * m * R2 * rx2 + 1) / 2);
   float *t1 = reinterpret_cast<float *>(T1.p()), *t2 = reinterpret_cast<float *>(T2.p());
-  gemm_f32(c, false, false, ry1 * R1, n * rx2, rx1, 1.f, PhiL, rx1, 0, x, n * rx2, 0, 0.f, t1, n * rx2, 0);
-  gemm_f32(c, true, false, m * R2, rx2, R1 * n, 1.f, Aajib, m * R2, 0, t1, rx2, (long long)R1 * n * rx2, 0.f, t2,
-           rx2, (long long)m * R2 * rx2, ry1);
-  gemm_f32(c, false, true, ry1 * m, ry2, R2 * rx2, 1.f, t2, R2 * rx2, 0, PhiR, R2 * rx2, 0, 0.f, y, ry2, 0);
+  auto g = tc ? gemm_f32_tc : gemm_f32;
+  g(c, false, false, ry1 * R1, n * rx2, rx1, 1.f, PhiL, rx1, 0, x, n * rx2, 0, 0.f, t1, n * rx2, 0, 1);
+  g(c, true, false, m * R2, rx2, R1 * n, 1.f, Aajib, m * R2, 0, t1, rx2, (long long)R1 * n * rx2, 0.f, t2, rx2,
+    (long long)m * R2 * rx2, ry1);
+  g(c, false, true, ry1 * m, ry2, R2 * rx2, 1.f, t2, R2 * rx2, 0, PhiR, R2 * rx2, 0, 0.f, y, ry2, 0, 1);
   c->flops32 += contraction_flops_local(ry1, R1, rx1, n, m, R2, rx2, ry2);
 }
 
@@ -375,8 +378,10 @@ void amen_solve(Ctx *c, TTOp &Aop, const TT &b, TT &x, double eps, int rmax, int
                 SolveStats *st, int prec) {
   TT &A = Aop.t;
   Aop.prepare(c);
-  const bool mixed = prec == TT_FP32_REFINED;
+  const bool use_tc = prec == TT_TF32_SPLIT;
+  const bool mixed = prec == TT_FP32_REFINED || use_tc;
   if (mixed) Aop.prepare32(c);
+  if (use_tc) TT_CHECK_CUDA(cudaMemsetAsync(c->d_scalar + 8, 0, sizeof(int), c->stream));
   const int d = A.d;
   TT_REQUIRE(b.d == d && x.d == d, "amen_solve: dimension mismatch");
   for (int k = 0; k < d; ++k)
@@ -439,7 +444,7 @@ void amen_solve(Ctx *c, TTOp &Aop, const TT &b, TT &x, double eps, int rmax, int
         const float *A32 = reinterpret_cast<const float *>(Aop.a_ajib32[k].p());
         auto mv32 = [&](const float *in, float *out) {
           local_matvec32(c, reinterpret_cast<const float *>(PL32.p()), A32, reinterpret_cast<const float *>(PR32.p()),
-                         in, r0, R1, r0, m, m, R2, r1, r1, out, T1, T2);
+                         in, r0, R1, r0, m, m, R2, r1, r1, out, T1, T2, use_tc);
         };
         r32.ensure(c, (N + 1) / 2);
         d32.ensure(c, (N + 1) / 2);
@@ -472,7 +477,7 @@ void amen_solve(Ctx *c, TTOp &Aop, const TT &b, TT &x, double eps, int rmax, int
       SVD s;
       {
         PhaseTimer pt(c, "amen.svd");
-        svd_rm(c, sol.p(), r0 * m, r1, s);
+        svd_rm(c, sol.p(), r0 * m, r1, s, SVD_ORTH_ANY);
       }
       double sn2 = 0;
       for (double v : s.Sh) sn2 += v * v;
@@ -484,6 +489,7 @@ void amen_solve(Ctx *c, TTOp &Aop, const TT &b, TT &x, double eps, int rmax, int
       solt.ensure(c, N);
       gemm(c, true, false, r0 * m, r1, rk, 1.0, s.Ut.p(), r0 * m, 0, v.p(), r1, 0, 0.0, solt.p(), r1, 0);
       const int rz0 = z.r[k], rz1 = z.r[k + 1];
+      PhaseTimer pt_res(c, "amen.residual");
       // crz = x'b z - x'Ax z . solt     (r0, m, rz1)
       crz.ensure(c, (size_t)r0 * m * rz1);
       vlocal(c, QX.L[k].p(), b.core[k].p(), QZ.R[k + 1].p(), r0, b.r[k], m, b.r[k + 1], rz1, crz.p(), T3);
@@ -504,6 +510,7 @@ void amen_solve(Ctx *c, TTOp &Aop, const TT &b, TT &x, double eps, int rmax, int
         split_enrich(c, x, k, s, rk, crz.p(), rz1);
       }
       const int nr1 = x.r[k + 1];
+      PhaseTimer pt_if(c, "amen.iface");
       left_update(c, PX.L[k].p(), x.core[k].p(), Aop.a_ajib[k].p(), x.core[k].p(), r0, R1, r0, m, m, R2, nr1, nr1,
                   PX.L[k + 1], T1, T2);
       vleft_update(c, QX.L[k].p(), x.core[k].p(), b.core[k].p(), r0, b.r[k], m, nr1, b.r[k + 1], QX.L[k + 1], T3);
@@ -522,6 +529,8 @@ void amen_solve(Ctx *c, TTOp &Aop, const TT &b, TT &x, double eps, int rmax, int
       right_all();
     }
   }
+  if (use_tc && tc_error_flag(c))
+    throw Error(TT_ETIMEOUT, "amen_solve: a tensor-core GEMM gave up waiting for its MMAs");
   if (st) {
     st->sweeps = std::min(swp, nswp);
     st->max_dx = maxdx;
@@ -585,7 +594,7 @@ void amen_mv(Ctx *c, TTOp &Aop, const TT &xin, TT &y, double eps, int rmax, int 
       SVD s;
       {
         PhaseTimer pt(c, "amen.svd");
-        svd_rm(c, sol.p(), r0 * m, r1, s);
+        svd_rm(c, sol.p(), r0 * m, r1, s, SVD_ORTH_ANY);
       }
       double sn2 = 0;
       for (double v : s.Sh) sn2 += v * v;

@@ -130,6 +130,7 @@ int tt_ctx_create(tt_ctx **out, void *stream) {
     uint64_t thr = UINT64_MAX;
     TT_CHECK_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
     TT_CHECK_CUDA(cudaMalloc(&ctx->c.d_scalar, 64 * sizeof(double)));
+    TT_CHECK_CUDA(cudaMemset(ctx->c.d_scalar, 0, 64 * sizeof(double)));
     TT_CHECK_CUDA(cudaMallocHost(&ctx->c.h_pinned, 4096 * sizeof(double)));
   });
   if (rc != TT_OK) {
@@ -145,6 +146,7 @@ int tt_ctx_destroy(tt_ctx *ctx) {
   cudaStreamSynchronize(ctx->c.stream);
   ctx->c.ws_gemm.release();
   ctx->c.ws_gemm32.release();
+  ctx->c.ws_tc.release();
   for (auto &s : ctx->c.scratch) s.release();
   cudaStreamSynchronize(ctx->c.stream);
   if (ctx->c.d_scalar) cudaFree(ctx->c.d_scalar);
@@ -177,9 +179,9 @@ int tt_ctx_set_profiling(tt_ctx *ctx, int on) {
   return guarded(ctx, [&] {
     ctx->c.prof_fold();
     ctx->c.profiling = on != 0;
-    ctx->c.gemm_flops = ctx->c.gemm32_flops = 0.0;
-    ctx->c.gemm_launches = ctx->c.gemm32_launches = 0;
-    ctx->c.gemm_ms_done = ctx->c.gemm32_ms_done = 0.0;
+    ctx->c.gemm_flops = ctx->c.gemm32_flops = ctx->c.gemmtc_flops = 0.0;
+    ctx->c.gemm_launches = ctx->c.gemm32_launches = ctx->c.gemmtc_launches = 0;
+    ctx->c.gemm_ms_done = ctx->c.gemm32_ms_done = ctx->c.gemmtc_ms_done = 0.0;
   });
 }
 
@@ -189,6 +191,15 @@ int tt_ctx_gemm_stats(tt_ctx *ctx, int64_t *launches, double *ms, double *flops)
     if (launches) *launches = ctx->c.gemm_launches;
     if (ms) *ms = ctx->c.gemm_ms_done;
     if (flops) *flops = ctx->c.gemm_flops;
+  });
+}
+
+int tt_ctx_gemmtc_stats(tt_ctx *ctx, int64_t *launches, double *ms, double *flops) {
+  return guarded(ctx, [&] {
+    ctx->c.prof_fold();
+    if (launches) *launches = ctx->c.gemmtc_launches;
+    if (ms) *ms = ctx->c.gemmtc_ms_done;
+    if (flops) *flops = ctx->c.gemmtc_flops;
   });
 }
 
@@ -409,7 +420,8 @@ int tt_solve_local(tt_ctx *ctx, const tt_op *A, const tt_vec *b, tt_vec *x, doub
   int conv = 1;
   int rc = guarded(ctx, [&] {
     TT_REQUIRE(A && b && x, "null argument");
-    TT_REQUIRE(prec == TT_FP64 || prec == TT_FP32_REFINED, "tt_solve_local: prec must be TT_FP64 or TT_FP32_REFINED");
+    TT_REQUIRE(prec == TT_FP64 || prec == TT_FP32_REFINED || prec == TT_TF32_SPLIT,
+               "tt_solve_local: prec must be TT_FP64, TT_FP32_REFINED or TT_TF32_SPLIT");
     TT_REQUIRE(eps > 0 && eps < 1, "tt_solve_local: eps in (0, 1)");
     TT_REQUIRE(max_sweeps >= 1 && kick >= 0, "tt_solve_local: bad sweeps/kick");
     tt_op *Am = const_cast<tt_op *>(A);
@@ -485,8 +497,8 @@ using clk = std::chrono::steady_clock;
 
 void check_opts(const keig_opts *opts) {
   TT_REQUIRE(opts, "null options");
-  TT_REQUIRE(opts->prec == TT_FP64 || opts->prec == TT_FP32_REFINED,
-             "keig: prec must be TT_FP64 or TT_FP32_REFINED");
+  TT_REQUIRE(opts->prec == TT_FP64 || opts->prec == TT_FP32_REFINED || opts->prec == TT_TF32_SPLIT,
+             "keig: prec must be TT_FP64, TT_FP32_REFINED or TT_TF32_SPLIT");
   TT_REQUIRE(opts->eps > 0 && opts->eps < 1 && opts->max_iter >= 1, "keig: bad eps/max_iter");
   TT_REQUIRE(opts->scheme == 0 || opts->scheme == 1, "keig: scheme must be 0 or 1");
 }
@@ -587,7 +599,8 @@ bool run_fixed_point(tt::Ctx *c, KeigOps &ops, const keig_opts *opts, keig_resul
     }
   }
   if (c->phase_timing) {
-    for (auto &p : c->phase_ms) fprintf(stderr, "phase %-22s %10.1f ms\n", p.first.c_str(), p.second);
+    for (auto &p : c->phase_ms)
+      fprintf(stderr, "phase %-22s %10.1f ms %8lld calls\n", p.name.c_str(), p.ms, p.calls);
     c->phase_ms.clear();
   }
   out->k = k;

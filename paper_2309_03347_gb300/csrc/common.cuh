@@ -95,10 +95,11 @@ struct Ctx {
   bool profiling = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
   size_t ev_used = 0;
-  std::vector<int> ev_tag;  // 0: FP64 GEMM, 1: FP32 GEMM
-  double gemm_flops = 0.0, gemm32_flops = 0.0;
-  int64_t gemm_launches = 0, gemm32_launches = 0;
-  double gemm_ms_done = 0.0, gemm32_ms_done = 0.0;  // folded-in time of events already read
+  std::vector<int> ev_tag;  // 0: FP64 GEMM, 1: FP32 GEMM, 2: tcgen05 TF32 GEMM
+  double gemm_flops = 0.0, gemm32_flops = 0.0, gemmtc_flops = 0.0;
+  int64_t gemm_launches = 0, gemm32_launches = 0, gemmtc_launches = 0;
+  double gemm_ms_done = 0.0, gemm32_ms_done = 0.0, gemmtc_ms_done = 0.0;  // folded-in event times
+  DBuf ws_tc;  // split-K partial sums of the tensor-core GEMM
   void prof_begin(cudaEvent_t *b, cudaEvent_t *e, int tag = 0);
   void prof_fold();
   double *h_pinned = nullptr;  // pinned host staging (4096 doubles)
@@ -106,14 +107,20 @@ struct Ctx {
   // host-side phase timers (enabled by the KEIG_PHASE_TIMES environment variable)
   bool phase_timing = false;
   bool mixed_svd = true;  // KEIG_FP64_SVD disables the FP32-preconditioned Jacobi
-  std::vector<std::pair<std::string, double>> phase_ms;
+  struct Phase {
+    std::string name;
+    double ms;
+    long long calls;
+  };
+  std::vector<Phase> phase_ms;
   void phase_add(const char *name, double ms) {
     for (auto &p : phase_ms)
-      if (p.first == name) {
-        p.second += ms;
+      if (p.name == name) {
+        p.ms += ms;
+        ++p.calls;
         return;
       }
-    phase_ms.push_back({name, ms});
+    phase_ms.push_back({name, ms, 1});
   }
   void count(int n = 1) { launches += n; }
 };
@@ -158,6 +165,11 @@ bool has_nonfinite(Ctx *c, const double *x, size_t n);
 // FP32 counterparts used by the mixed-precision local solves
 void gemm_f32(Ctx *c, bool ta, bool tb, int M, int N, int K, float alpha, const float *A, int lda, long long sA,
               const float *B, int ldb, long long sB, float beta, float *C, int ldc, long long sC, int batch = 1);
+// the same product on the tcgen05 tensor cores (kind::tf32, three-term split; tc_gemm.cu)
+void gemm_f32_tc(Ctx *c, bool ta, bool tb, int M, int N, int K, float alpha, const float *A, int lda, long long sA,
+                 const float *B, int ldb, long long sB, float beta, float *C, int ldc, long long sC, int batch = 1);
+// nonzero when a tensor-core GEMM gave up a bounded wait (reads device memory)
+int tc_error_flag(Ctx *c);
 void d2f(Ctx *c, const double *x, float *y, size_t n, double s = 1.0);
 void f2d_axpy(Ctx *c, const float *x, double *y, size_t n, double a);
 void axpby_f(Ctx *c, size_t n, float a, const float *x, float b, float *y);
@@ -171,9 +183,11 @@ void qr_colmajor(Ctx *c, double *A, int m, int n, double *Q, double *R);
 // One-sided Jacobi SVD of a column-major square n x n matrix (destroyed):
 // U (n x n), V (n x n) column-major and S (n) sorted by decreasing value.
 void jacobi_svd(Ctx *c, double *B, int n, double *U, double *S, double *V);
-// Same contract, rotations found in FP32 then polished in FP64 (svd_mixed.cu).
+// Same product B = U S V^T with rotations found in FP32 and refined by FP64
+// matrix products (svd_mixed.cu): V orthonormal to FP64 rounding (U when
+// exact_u), the other factor up to the cosines between near pairs.
 bool jacobi_svd_mixed_fits(int n);
-void jacobi_svd_mixed(Ctx *c, double *B, int n, double *U, double *S, double *V);
+void jacobi_svd_mixed(Ctx *c, double *B, int n, double *U, double *S, double *V, bool exact_u);
 
 // Kronecker core product of the exact TT matvec:
 // Y[(a,b), i, (c,e)] = sum_j A[a,i,j,c] X[b,j,e]

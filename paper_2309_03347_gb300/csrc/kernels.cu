@@ -69,7 +69,7 @@ void Ctx::prof_fold() {
   for (size_t i = 0; i < ev_used; ++i) {
     float ms = 0.f;
     TT_CHECK_CUDA(cudaEventElapsedTime(&ms, ev_pool[i].first, ev_pool[i].second));
-    (ev_tag[i] ? gemm32_ms_done : gemm_ms_done) += ms;
+    (ev_tag[i] == 2 ? gemmtc_ms_done : ev_tag[i] == 1 ? gemm32_ms_done : gemm_ms_done) += ms;
   }
   ev_used = 0;
 }
@@ -600,27 +600,34 @@ void qr_colmajor(Ctx *c, double *A, int m, int n, double *Q, double *R) {
 // the round-robin pair ordering; rotation from the classical formulas
 // zeta = (beta - alpha) / (2 gamma), t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)).
 // The matrix is staged in shared memory when it fits, V stays in global memory.
-constexpr int JAC_THREADS = 512;
+constexpr int JAC_THREADS = 1024;
 constexpr int JAC_SMEM_DOUBLES = 24 * 1024;  // 192 KB
 constexpr int JAC_MAX_SWEEPS = 40;
 
+// One-sided (Hestenes) Jacobi SVD of an n x n column-major matrix on one CTA:
+// one warp per column pair of a round-robin round, B (and V when both fit)
+// in shared memory.  A pair is rotated while its columns' cosine exceeds
+// n * 2^-52, the level below which FP64 rounding of the dot products makes
+// the cosine noise (a tighter threshold never stops rotating).
 __global__ void __launch_bounds__(JAC_THREADS) jacobi_svd_kernel(double *__restrict__ Bg, int n,
                                                                  double *__restrict__ U,
                                                                  double *__restrict__ S,
                                                                  double *__restrict__ V,
-                                                                 double *__restrict__ Vtmp,
-                                                                 int use_smem) {
+                                                                 double *__restrict__ Vscr,
+                                                                 int smem_mode) {
   extern __shared__ double smem[];
   __shared__ int s_rot;
-  double *B = use_smem ? smem : Bg;
   const long long nn = (long long)n * n;
-  if (use_smem)
+  // smem_mode: 0 both in global memory, 1 B in shared memory, 2 B and V in shared memory
+  double *B = smem_mode >= 1 ? smem : Bg;
+  double *Vtmp = smem_mode == 2 ? smem + nn : Vscr;
+  if (smem_mode >= 1)
     for (long long e = threadIdx.x; e < nn; e += blockDim.x) B[e] = Bg[e];
   for (long long e = threadIdx.x; e < nn; e += blockDim.x) Vtmp[e] = ((e % n) == (e / n)) ? 1.0 : 0.0;
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   const int np = (n + 1) & ~1;  // players (padded to even)
-  const double tol = 1e-15;
+  const double tol = fmax(1e-15, 2.220446049250313e-16 * n);
   for (int sweep = 0; sweep < JAC_MAX_SWEEPS; ++sweep) {
     if (threadIdx.x == 0) s_rot = 0;
     __syncthreads();
@@ -676,7 +683,7 @@ __global__ void __launch_bounds__(JAC_THREADS) jacobi_svd_kernel(double *__restr
     __syncthreads();
   }
   // singular values = column norms; sort descending (rank by counting, ties by index)
-  double *sv = Vtmp + nn;  // n scratch doubles after Vtmp
+  double *sv = Vscr + nn;  // n scratch doubles after the V scratch
   for (int j = warp; j < n; j += nwarp) {
     const double *bj = B + (long long)j * n;
     double s = 0.0;
@@ -705,12 +712,13 @@ __global__ void __launch_bounds__(JAC_THREADS) jacobi_svd_kernel(double *__restr
 void jacobi_svd(Ctx *c, double *B, int n, double *U, double *S, double *V) {
   TT_REQUIRE(n > 0, "jacobi_svd: empty");
   c->scratch[5].ensure(c, (size_t)n * n + n);
-  const bool sm = (long long)n * n <= JAC_SMEM_DOUBLES;
-  const size_t bytes = sm ? (size_t)n * n * sizeof(double) : 0;
-  if (sm)
+  const long long nn = (long long)n * n;
+  const int mode = 2 * nn <= JAC_SMEM_DOUBLES ? 2 : nn <= JAC_SMEM_DOUBLES ? 1 : 0;
+  const size_t bytes = (size_t)mode * nn * sizeof(double);
+  if (mode)
     TT_CHECK_CUDA(cudaFuncSetAttribute(jacobi_svd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)(JAC_SMEM_DOUBLES * sizeof(double))));
-  jacobi_svd_kernel<<<1, JAC_THREADS, bytes, c->stream>>>(B, n, U, S, V, c->scratch[5].p(), sm ? 1 : 0);
+  jacobi_svd_kernel<<<1, JAC_THREADS, bytes, c->stream>>>(B, n, U, S, V, c->scratch[5].p(), mode);
   LAUNCH_CHECK(c);
 }
 

@@ -52,13 +52,19 @@ void tt_check(const TT &x);
 
 // SVD of a row-major m x n device matrix A (not modified).  k = min(m, n).
 // Ut: k x m (rows = left singular vectors), Vt: k x n, S: k (device and host),
-// all sorted by decreasing singular value.
+// all sorted by decreasing singular value; A = Ut^T S Vt to FP64 rounding.
+// orth names the factor that must be orthonormal to FP64 rounding
+// (SVD_ORTH_U: Ut, SVD_ORTH_V: Vt); with the mixed-precision small SVD the
+// other factor is orthonormal only up to the cosines left between columns of
+// nearly equal singular values, which leaves the truncation error (the norm
+// of the dropped part) exact.
 struct SVD {
   int m = 0, n = 0, k = 0;
   DBuf Ut, Vt, S;
   std::vector<double> Sh;
 };
-void svd_rm(Ctx *c, const double *A, int m, int n, SVD &out);
+enum { SVD_ORTH_U = 1, SVD_ORTH_V = 2, SVD_ORTH_ANY = 3 };
+void svd_rm(Ctx *c, const double *A, int m, int n, SVD &out, int orth);
 int trunc_rank(const std::vector<double> &s, double delta, int rmax);
 
 // QR of a row-major m x n matrix A given as its transpose At (n x m

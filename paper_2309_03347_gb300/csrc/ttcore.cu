@@ -109,16 +109,17 @@ void qr_rm_from_t(Ctx *c, double *At, int m, int n, DBuf &Q, DBuf &R, int &k) {
   transpose(c, Rc.p(), R.p(), n, k);
 }
 
-// SVD of the small square R factor: mixed-precision Jacobi above 24 columns
-// (FP32 rotations, FP64 polish), plain FP64 Jacobi below.
-static void small_svd(Ctx *c, double *R, int k, double *U, double *S, double *V) {
+// SVD of the small square R factor: mixed precision above 24 columns (FP32
+// rotations refined by FP64 products), plain FP64 Jacobi below.  exact_u asks
+// for U orthonormal to FP64 rounding (V is, otherwise).
+static void small_svd(Ctx *c, double *R, int k, double *U, double *S, double *V, bool exact_u) {
   if (c->mixed_svd && k >= 24 && jacobi_svd_mixed_fits(k))
-    jacobi_svd_mixed(c, R, k, U, S, V);
+    jacobi_svd_mixed(c, R, k, U, S, V, exact_u);
   else
     jacobi_svd(c, R, k, U, S, V);
 }
 
-void svd_rm(Ctx *c, const double *A, int m, int n, SVD &o) {
+void svd_rm(Ctx *c, const double *A, int m, int n, SVD &o, int orth) {
   TT_REQUIRE(m > 0 && n > 0, "svd: empty matrix");
   o.m = m;
   o.n = n;
@@ -133,8 +134,14 @@ void svd_rm(Ctx *c, const double *A, int m, int n, SVD &o) {
     // X = A^T (n x m) column-major is A's memory: X = Q R, R = Ur S Vr^T
     // A = Vr S (Q Ur)^T  ->  Ut = Vr^T (Vr col-major memory), Vt = Ur^T Q^T
     copy(c, work.p(), A, (size_t)m * n);
-    qr_colmajor(c, work.p(), n, m, Q.p(), Rm.p());
-    small_svd(c, Rm.p(), k, Ur.p(), o.S.p(), Vr.p());
+    {
+      PhaseTimer pt(c, "svd.qr");
+      qr_colmajor(c, work.p(), n, m, Q.p(), Rm.p());
+    }
+    {
+      PhaseTimer pt(c, "svd.small");
+      small_svd(c, Rm.p(), k, Ur.p(), o.S.p(), Vr.p(), orth == SVD_ORTH_V);
+    }
     copy(c, o.Ut.p(), Vr.p(), (size_t)k * k);
     // Vt (k x n row-major) = Ur^T (row-major view of Ur col-major: k x k) * Q^T (row-major view k x n)
     gemm(c, false, false, k, n, k, 1.0, Ur.p(), k, 0, Q.p(), n, 0, 0.0, o.Vt.p(), n, 0);
@@ -142,8 +149,14 @@ void svd_rm(Ctx *c, const double *A, int m, int n, SVD &o) {
     // A column-major = transpose of memory: A = Q R, R = Ur S Vr^T
     // A = (Q Ur) S Vr^T -> Ut = Ur^T Q^T, Vt = Vr^T (Vr col-major memory)
     transpose(c, A, work.p(), m, n);
-    qr_colmajor(c, work.p(), m, n, Q.p(), Rm.p());
-    small_svd(c, Rm.p(), k, Ur.p(), o.S.p(), Vr.p());
+    {
+      PhaseTimer pt(c, "svd.qr");
+      qr_colmajor(c, work.p(), m, n, Q.p(), Rm.p());
+    }
+    {
+      PhaseTimer pt(c, "svd.small");
+      small_svd(c, Rm.p(), k, Ur.p(), o.S.p(), Vr.p(), orth == SVD_ORTH_U);
+    }
     gemm(c, false, false, k, m, k, 1.0, Ur.p(), k, 0, Q.p(), m, 0, 0.0, o.Ut.p(), m, 0);
     copy(c, o.Vt.p(), Vr.p(), (size_t)k * k);
   }
@@ -206,7 +219,7 @@ void round(Ctx *c, TT &x, double eps, int rmax) {
   for (int k = x.d - 1; k >= 1; --k) {
     const int r0 = x.r[k], cols = x.n[k] * x.r[k + 1];
     SVD s;
-    svd_rm(c, x.core[k].p(), r0, cols, s);
+    svd_rm(c, x.core[k].p(), r0, cols, s, SVD_ORTH_V);
     const int rk = trunc_rank(s.Sh, delta, rmax);
     DBuf nc(c, (size_t)rk * cols);
     copy(c, nc.p(), s.Vt.p(), (size_t)rk * cols);
@@ -401,7 +414,7 @@ TT tt_svd_dense(Ctx *c, const double *a, const std::vector<int> &modes, double e
     rest /= (size_t)modes[k];
     TT_REQUIRE(rest <= (size_t)INT32_MAX, "tt_svd: unfolding too large");
     SVD s;
-    svd_rm(c, cur.p(), rows, (int)rest, s);
+    svd_rm(c, cur.p(), rows, (int)rest, s, SVD_ORTH_U);
     const int rk = trunc_rank(s.Sh, delta, rmax);
     x.core[k].alloc(c, (size_t)rows * rk);
     transpose(c, s.Ut.p(), x.core[k].p(), rk, rows);

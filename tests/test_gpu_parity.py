@@ -112,8 +112,9 @@ def test_round_rank_cap(ctx):
 
 @pytest.mark.parametrize("eps", [0.0, 1e-9, 1e-4])
 def test_round_large_ranks(ctx, eps):
-    # bonds of 40-90 go through the FP32-preconditioned Jacobi with FP64
-    # polish; the result must still be an FP64-accurate rounding
+    # bonds of 40-90 go through the mixed-precision SVD (FP32 rotations
+    # refined by FP64 matrix products); the result must still be an
+    # FP64-accurate rounding
     modes = [4, 8, 6, 4, 4, 2]
     ranks = [1, 4, 32, 90, 48, 8, 1]
     c = ki.random_cores(modes, ranks, 17)
@@ -133,6 +134,22 @@ def test_round_large_ranks(ctx, eps):
     for k, core in enumerate(x.cores()[1:], start=1):
         m = core.reshape(core.shape[0], -1)
         assert np.abs(m @ m.T - np.eye(m.shape[0])).max() < 1e-12
+
+
+def test_round_large_redundant_ranks(ctx):
+    # x + x with bonds of 60-80: half of every bond's singular values are
+    # exactly zero; the mixed-precision SVD must resolve them to the FP64
+    # noise level so that rounding at 1e-14 returns the original ranks
+    modes = [4, 8, 6, 4, 4, 2]
+    ranks = [1, 4, 30, 40, 30, 8, 1]
+    c = ki.random_cores(modes, ranks, 23)
+    c = [ci * (0.9 ** np.arange(ci.shape[2]))[None, None, :] for ci in c]
+    x = _vec(ctx, c)
+    x.axpby(1.0, _vec(ctx, c), 1.0)
+    assert max(x.ranks) == 80
+    K.tt_round(ctx, x, 1e-14)
+    assert rel(x.dense_cuda().cpu().numpy(), 2 * R.full(c)) < 1e-12
+    assert x.ranks == R.ranks(R.tt_round(c, 1e-14))
 
 
 def _rand_op(modes, ranks, seed):
