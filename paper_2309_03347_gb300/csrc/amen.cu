@@ -226,90 +226,103 @@ int gmres(Ctx *c, Gmres &G, MV &&mv, const double *b, double *x, size_t N, doubl
 struct Gmres32 {
   int restart = 30;
   int maxit = 300;
-  DBuf V, hbuf, r, y;
-  std::vector<double> H, cs, sn, g;
+  DBuf V, r, dev;
+  std::vector<cudaEvent_t> ev;
+  Gmres32() = default;
+  Gmres32(const Gmres32 &) = delete;
+  Gmres32 &operator=(const Gmres32 &) = delete;
+  ~Gmres32() {
+    for (auto e : ev) cudaEventDestroy(e);
+  }
 };
 
+// Restarted GMRES in FP32 (classical Gram-Schmidt applied twice) for the
+// correction equation of the iterative refinement.  The Arnoldi state (H,
+// Givens rotations, residual estimate) lives on the device; the host queues
+// step j + 1 before it waits for the residual of step j, so the device runs
+// the steps back to back.  A step queued after convergence is discarded
+// (only columns up to the converged one enter the solution).  Returns the
+// number of steps run.
 template <class MV>
 int gmres32(Ctx *c, Gmres32 &G, MV &&mv, const float *b, float *x, size_t N, double tol) {
   const int mr = G.restart;
+  TT_REQUIRE(mr + 1 <= KRY_MAX_VECS && 2 * mr + 2 <= 1024, "gmres32: restart too long");
   G.V.ensure(c, ((size_t)(mr + 1) * N + 1) / 2);
-  G.hbuf.ensure(c, (size_t)2 * (mr + 1) + 4);
   G.r.ensure(c, (N + 1) / 2);
-  G.y.ensure(c, (size_t)mr + 1);
-  G.H.assign((size_t)(mr + 1) * mr, 0.0);
-  G.cs.assign(mr, 0.0);
-  G.sn.assign(mr, 0.0);
-  G.g.assign(mr + 1, 0.0);
+  // device state: H, cs, sn, g, y, st, inv, h1, h2, part1, part2, npart
+  const size_t oH = 0, ocs = oH + (size_t)(mr + 1) * mr, osn = ocs + mr, og = osn + mr, oy = og + mr + 1,
+               ost = oy + mr + 1, oinv = ost + 2 * mr + 2, oh1 = oinv + 1, oh2 = oh1 + mr + 1, op1 = oh2 + mr + 1,
+               op2 = op1 + (size_t)(mr + 1) * KRY_MAX_SPLIT, onp = op2 + (size_t)(mr + 1) * KRY_MAX_SPLIT,
+               total = onp + (size_t)c->sm_count * 4 + 1;
+  G.dev.ensure(c, total);
+  while ((int)G.ev.size() < mr) {
+    cudaEvent_t e;
+    TT_CHECK_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    G.ev.push_back(e);
+  }
+  double *D = G.dev.p();
+  double *H = D + oH, *cs = D + ocs, *sn = D + osn, *g = D + og, *y = D + oy, *st = D + ost, *inv = D + oinv,
+         *h1 = D + oh1, *h2 = D + oh2, *p1 = D + op1, *p2 = D + op2, *np = D + onp;
   float *V = reinterpret_cast<float *>(G.V.p());
   float *r = reinterpret_cast<float *>(G.r.p());
-  double *hd = G.hbuf.p();
-  double *hp = c->h_pinned;
+  double *hp = c->h_pinned + 2048;  // landing area of the per-step status (2 mr + 2 doubles)
   int it = 0;
   TT_CHECK_CUDA(cudaMemsetAsync(x, 0, N * sizeof(float), c->stream));
+  auto step = [&](int j) {
+    float *w = V + (size_t)(j + 1) * N;
+    mv(V + (size_t)j * N, w);
+    int S = kry_mdot(c, V, N, j + 1, w, N, p1);
+    kry_maxpy(c, V, N, j + 1, p1, S, w, N, h1, nullptr);
+    S = kry_mdot(c, V, N, j + 1, w, N, p2);
+    const int nb = kry_maxpy(c, V, N, j + 1, p2, S, w, N, h2, np);
+    kry_arnoldi(c, j, mr, h1, h2, np, nb, H, cs, sn, g, st, inv);
+    kry_scale(c, w, w, N, inv);
+    TT_CHECK_CUDA(cudaMemcpyAsync(hp + 2 * j, st + 2 * j, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    TT_CHECK_CUDA(cudaEventRecord(G.ev[j], c->stream));
+  };
+  // true when step j ended the cycle (converged or broke down)
+  auto finished = [&](int j) {
+    TT_CHECK_CUDA(cudaEventSynchronize(G.ev[j]));
+    const double res = hp[2 * j], hn = hp[2 * j + 1];
+    if (!std::isfinite(hn) || !std::isfinite(res)) throw Error(TT_ENONFINITE, "gmres32: non-finite Krylov vector");
+    return res <= tol || hn <= 1e-30;
+  };
   while (true) {
-    // r = b - M x
+    // r = b - M x ; beta = ||r||
     mv(x, r);
     axpby_f(c, N, 1.f, b, -1.f, r);
-    dot_f_dev(c, r, r, N, hd);
-    TT_CHECK_CUDA(cudaMemcpyAsync(hp, hd, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    const int nb = kry_sumsq(c, r, N, np);
+    kry_start(c, np, nb, mr, g, st, inv);
+    TT_CHECK_CUDA(cudaMemcpyAsync(hp + 2 * mr, st, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     c->sync();
-    const double beta = std::sqrt(std::max(hp[0], 0.0));
+    const double beta = hp[2 * mr];
+    if (!std::isfinite(beta)) throw Error(TT_ENONFINITE, "gmres32: non-finite residual");
     if (!(beta > tol) || it >= G.maxit) return it;
-    axpby_f(c, N, (float)(1.0 / beta), r, 0.f, V);
-    std::fill(G.g.begin(), G.g.end(), 0.0);
-    G.g[0] = beta;
-    int jend = -1;
-    double res = beta;
+    kry_scale(c, r, V, N, inv);
+    int jend = 0;
+    bool done = false;
+    step(0);
+    ++it;
     for (int j = 0; j < mr; ++j) {
-      float *w = V + (size_t)(j + 1) * N;
-      mv(V + (size_t)j * N, w);
-      ++it;
-      multi_dot_f(c, V, N, j + 1, w, N, hd);
-      multi_axpy_f(c, V, N, j + 1, hd, w, N);
-      multi_dot_f(c, V, N, j + 1, w, N, hd + (mr + 1));
-      multi_axpy_f(c, V, N, j + 1, hd + (mr + 1), w, N);
-      dot_f_dev(c, w, w, N, hd + 2 * (mr + 1));
-      TT_CHECK_CUDA(cudaMemcpyAsync(hp, hd, sizeof(double) * (2 * (mr + 1) + 1), cudaMemcpyDeviceToHost,
-                                    c->stream));
-      c->sync();
-      const double hn = std::sqrt(std::max(hp[2 * (mr + 1)], 0.0));
-      double *Hc = &G.H[0];
-      for (int i = 0; i <= j; ++i) Hc[(size_t)i * mr + j] = hp[i] + hp[(mr + 1) + i];
-      Hc[(size_t)(j + 1) * mr + j] = hn;
-      if (!std::isfinite(hn)) throw Error(TT_ENONFINITE, "gmres32: non-finite Krylov vector");
-      for (int i = 0; i < j; ++i) {
-        const double a = Hc[(size_t)i * mr + j], bb = Hc[(size_t)(i + 1) * mr + j];
-        Hc[(size_t)i * mr + j] = G.cs[i] * a + G.sn[i] * bb;
-        Hc[(size_t)(i + 1) * mr + j] = -G.sn[i] * a + G.cs[i] * bb;
+      const bool more = j + 1 < mr && it < G.maxit;
+      if (more) {
+        step(j + 1);
+        ++it;
       }
-      const double a = Hc[(size_t)j * mr + j], bb = Hc[(size_t)(j + 1) * mr + j];
-      const double den = std::hypot(a, bb);
-      G.cs[j] = den == 0.0 ? 1.0 : a / den;
-      G.sn[j] = den == 0.0 ? 0.0 : bb / den;
-      Hc[(size_t)j * mr + j] = den;
-      Hc[(size_t)(j + 1) * mr + j] = 0.0;
-      G.g[j + 1] = -G.sn[j] * G.g[j];
-      G.g[j] = G.cs[j] * G.g[j];
-      res = std::fabs(G.g[j + 1]);
-      jend = j;
-      const bool breakdown = hn <= 1e-30;
-      if (!breakdown) axpby_f(c, N, (float)(1.0 / hn), w, 0.f, w);
-      if (res <= tol || it >= G.maxit || breakdown) break;
+      const bool fin = finished(j);
+      if (fin || !more) {
+        jend = j;
+        done = fin || it >= G.maxit;
+        break;
+      }
     }
-    const int kk = jend + 1;
-    std::vector<double> yv(kk, 0.0);
-    for (int i = kk - 1; i >= 0; --i) {
-      double s = G.g[i];
-      for (int l = i + 1; l < kk; ++l) s -= G.H[(size_t)i * mr + l] * yv[l];
-      const double dgl = G.H[(size_t)i * mr + i];
-      yv[i] = dgl != 0.0 ? s / dgl : 0.0;
+    // x += V y,  y = H^-1 g over the columns 0..jend
+    kry_trisolve(c, jend + 1, mr, H, g, y);
+    multi_axpy_f(c, V, N, jend + 1, y, x, N);
+    if (done) {
+      c->sync();
+      return it;
     }
-    for (int i = 0; i < kk; ++i) hp[i] = -yv[i];
-    TT_CHECK_CUDA(cudaMemcpyAsync(G.y.p(), hp, sizeof(double) * kk, cudaMemcpyHostToDevice, c->stream));
-    multi_axpy_f(c, V, N, kk, G.y.p(), x, N);  // x += V y
-    c->sync();
-    if (res <= tol || it >= G.maxit) return it;
   }
 }
 
@@ -412,6 +425,7 @@ void amen_solve(Ctx *c, TTOp &Aop, const TT &b, TT &x, double eps, int rmax, int
   right_all();
   Gmres G;
   Gmres32 G32;
+  PGWork PGW;
   DBuf rhs, sol, solt, crz, czz, tmp, PL32, PR32, r32, d32, r64;
   double maxdx = 0.0;
   int swp = 0;
@@ -457,8 +471,14 @@ void amen_solve(Ctx *c, TTOp &Aop, const TT &b, TT &x, double eps, int rmax, int
           if (!(nrr > loc_eps * nb)) break;
           d2f(c, r64.p(), reinterpret_cast<float *>(r32.p()), N, 1.0 / nrr);
           const double tol_in = std::max(0.3 * loc_eps * nb / nrr, 2e-6);
-          git += gmres32(c, G32, mv32, reinterpret_cast<const float *>(r32.p()), reinterpret_cast<float *>(d32.p()),
-                         N, tol_in);
+          if (!use_tc && c->persistent_gmres && pgmres32_fits(c, (int)N, G32.restart))
+            git += pgmres32(c, reinterpret_cast<const float *>(PL32.p()), A32,
+                            reinterpret_cast<const float *>(PR32.p()), r0, R1, m, R2, r1,
+                            reinterpret_cast<const float *>(r32.p()), reinterpret_cast<float *>(d32.p()), tol_in,
+                            G32.restart, G32.maxit, PGW);
+          else
+            git += gmres32(c, G32, mv32, reinterpret_cast<const float *>(r32.p()),
+                           reinterpret_cast<float *>(d32.p()), N, tol_in);
           f2d_axpy(c, reinterpret_cast<const float *>(d32.p()), sol.p(), N, nrr);
         }
       }

@@ -124,6 +124,7 @@ int tt_ctx_create(tt_ctx **out, void *stream) {
     ctx->c.stream = (cudaStream_t)stream;
     ctx->c.phase_timing = getenv("KEIG_PHASE_TIMES") != nullptr;
     ctx->c.mixed_svd = getenv("KEIG_FP64_SVD") == nullptr;
+    ctx->c.persistent_gmres = getenv("KEIG_LAUNCHED_GMRES") == nullptr;
     // keep freed blocks in the stream-ordered pool
     cudaMemPool_t pool;
     TT_CHECK_CUDA(cudaDeviceGetDefaultMemPool(&pool, ctx->c.device));

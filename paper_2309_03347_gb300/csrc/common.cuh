@@ -107,6 +107,7 @@ struct Ctx {
   // host-side phase timers (enabled by the KEIG_PHASE_TIMES environment variable)
   bool phase_timing = false;
   bool mixed_svd = true;  // KEIG_FP64_SVD disables the FP32-preconditioned Jacobi
+  bool persistent_gmres = true;  // KEIG_LAUNCHED_GMRES selects the per-step-launch FP32 GMRES
   struct Phase {
     std::string name;
     double ms;
@@ -176,6 +177,36 @@ void axpby_f(Ctx *c, size_t n, float a, const float *x, float b, float *y);
 void multi_dot_f(Ctx *c, const float *V, size_t ldv, int nv, const float *w, size_t n, double *h);
 void multi_axpy_f(Ctx *c, const float *V, size_t ldv, int nv, const double *h, float *w, size_t n);
 void dot_f_dev(Ctx *c, const float *x, const float *y, size_t n, double *out);
+
+// Device-resident steps of the FP32 GMRES (krylov.cu).  Vectors are FP32
+// columns of V with stride ldv; reductions accumulate in FP64.
+constexpr int KRY_MAX_VECS = 64;   // basis vectors per Gram-Schmidt product
+constexpr int KRY_MAX_SPLIT = 32;  // CTAs per vector in kry_mdot
+// part[j S + s] = partial V_j . w; returns S (part holds nv * S doubles)
+int kry_mdot(Ctx *c, const float *V, size_t ldv, int nv, const float *w, size_t n, double *part);
+// w -= sum_j h_j V_j with h_j = sum_s part[j S + s]; hout (nv) = h if given;
+// npart (returned count) = per-CTA sums of the new w^2 if given
+int kry_maxpy(Ctx *c, const float *V, size_t ldv, int nv, const double *part, int S, float *w, size_t n,
+              double *hout, double *npart);
+// per-CTA partial sums of x^2; returns their count (<= 4 x SMs)
+int kry_sumsq(Ctx *c, const float *x, size_t n, double *npart);
+// Arnoldi step j of a cycle with restart mr (see krylov.cu)
+void kry_arnoldi(Ctx *c, int j, int mr, const double *h1, const double *h2, const double *npart, int nb, double *H,
+                 double *cs, double *sn, double *g, double *st, double *inv);
+void kry_start(Ctx *c, const double *npart, int nb, int mr, double *g, double *st, double *inv);
+void kry_trisolve(Ctx *c, int kk, int mr, const double *H, const double *g, double *y);
+// y = s[0] x (s on the device; x == y allowed)
+void kry_scale(Ctx *c, const float *x, float *y, size_t n, const double *s);
+
+// Restarted FP32 GMRES of the local system Phi_L A Phi_R (FP32 operands,
+// square: row and column ranks r0, r1, mode m) as one persistent cooperative
+// kernel (pgmres.cu); x = solution from x0 = 0.  Returns the Arnoldi steps.
+struct PGWork {
+  DBuf V, T1, T2, ws, D, st;
+};
+bool pgmres32_fits(Ctx *c, int N, int restart);
+int pgmres32(Ctx *c, const float *PL, const float *A32, const float *PR, int r0, int R1, int m, int R2, int r1,
+             const float *b, float *x, double tol, int restart, int maxit, PGWork &W);
 
 // Householder QR of column-major A (m x n, lda = m), overwritten by the
 // reflectors; Q (m x k, k = min(m,n)) and R (k x n) written column-major.
