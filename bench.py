@@ -267,6 +267,7 @@ def main():
     n_gemm, gemm_ms, gemm_flops = ctx.gemm_stats()
     n32, gemm32_ms, gemm32_flops = ctx.gemm32_stats()
     ntc, gemmtc_ms, gemmtc_flops = ctx.gemmtc_stats()
+    npg, pg_ms, pg_flops = ctx.gmres_stats()
     ctx.set_profiling(False)
 
     if rank != 0:
@@ -302,8 +303,11 @@ def main():
     tf32_peak, tf32_src = tf32_tensor_peak_tflops()
     rtc = roof("tc_gemm_kernel (tcgen05 TF32 three-term contraction GEMM; 3 MMA passes per product, "
                "so frac <= 1/3)", ntc, gemmtc_ms, gemmtc_flops, tf32_peak, tf32_src, bound="tensor")
+    rpg = roof("pgmres_kernel (persistent FP32 GMRES of the local systems: local matvecs + Gram-Schmidt)", npg,
+               pg_ms, pg_flops, fp32_simt_peak_tflops(sm_max),
+               "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock (MEASURED_PEAKS.json has no FP32 entry)")
     # the dominant contraction kernel of the step (by device time) carries the roofline
-    roofs = sorted([(gemm_ms, r64), (gemm32_ms, r32), (gemmtc_ms, rtc)], key=lambda t: -t[0])
+    roofs = sorted([(gemm_ms, r64), (gemm32_ms, r32), (gemmtc_ms, rtc), (pg_ms, rpg)], key=lambda t: -t[0])
     line["roofline"] = roofs[0][1]
     line["roofline_other_gemm"] = [r for t, r in roofs[1:] if r["launches"]]
     line["contraction_tflops_step"] = cflops / max(args.steps, 1) / (ms_step * 1e-3) / 1e12

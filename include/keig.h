@@ -66,9 +66,9 @@ const char *tt_last_error(const tt_ctx *ctx);
 /* Library version string (static storage). */
 const char *tt_version(void);
 /* Counters since creation or the last reset: kernel launches issued by the
- * library and algorithmic FP64 flops of the core contractions (the
- * operator-core x vector-core products: exact matvec, local-system matvecs
- * and interface updates). */
+ * library and algorithmic flops of the core contractions (the operator-core
+ * x vector-core products: exact matvec, local-system matvecs and interface
+ * updates), in FP64 and, for the mixed-precision solves, FP32 together. */
 int tt_ctx_counters(tt_ctx *ctx, int64_t *launches, double *contraction_flops);
 int tt_ctx_reset_counters(tt_ctx *ctx);
 /* Per-launch timing of the dense contraction kernel (the FP64 GEMM that all
@@ -84,6 +84,10 @@ int tt_ctx_gemm32_stats(tt_ctx *ctx, int64_t *launches, double *ms, double *flop
 /* The same for the tcgen05 TF32 three-term GEMM of TT_TF32_SPLIT (flops
  * counted algorithmically, 2 M N K per product, not per MMA pass). */
 int tt_ctx_gemmtc_stats(tt_ctx *ctx, int64_t *launches, double *ms, double *flops);
+/* The same for the persistent FP32 GMRES kernel of the TT_FP32_REFINED local
+ * solves (one launch per correction solve); flops = the local matvecs at
+ * 2 n r0 r1 (r0 R1 + n R1 R2 + r1 R2) each plus the Gram-Schmidt passes. */
+int tt_ctx_gmres_stats(tt_ctx *ctx, int64_t *launches, double *ms, double *flops);
 
 /* ---------------------------------------------------------------- TT vectors */
 

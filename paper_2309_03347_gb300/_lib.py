@@ -79,6 +79,7 @@ def load():
             "tt_ctx_gemm_stats": ([P, C.POINTER(C.c_int64), D, D], C.c_int),
             "tt_ctx_gemm32_stats": ([P, C.POINTER(C.c_int64), D, D], C.c_int),
             "tt_ctx_gemmtc_stats": ([P, C.POINTER(C.c_int64), D, D], C.c_int),
+            "tt_ctx_gmres_stats": ([P, C.POINTER(C.c_int64), D, D], C.c_int),
             "tt_vec_create": ([P, C.c_int, I, I, D, C.c_int, C.POINTER(P)], C.c_int),
             "tt_vec_destroy": ([P], C.c_int),
             "tt_vec_shape": ([P, I, I, I], C.c_int),
@@ -176,6 +177,13 @@ class Context:
         ms = C.c_double()
         f = C.c_double()
         self.check(self.lib.tt_ctx_gemm_stats(self.h, C.byref(n), C.byref(ms), C.byref(f)))
+        return int(n.value), float(ms.value), float(f.value)
+
+    def gmres_stats(self):
+        n = C.c_int64()
+        ms = C.c_double()
+        f = C.c_double()
+        self.check(self.lib.tt_ctx_gmres_stats(self.h, C.byref(n), C.byref(ms), C.byref(f)))
         return int(n.value), float(ms.value), float(f.value)
 
     def gemmtc_stats(self):

@@ -165,7 +165,7 @@ const char *tt_last_error(const tt_ctx *ctx) { return ctx ? ctx->c.err.c_str() :
 int tt_ctx_counters(tt_ctx *ctx, int64_t *launches, double *flops) {
   if (!ctx) return TT_EINVAL;
   if (launches) *launches = ctx->c.launches;
-  if (flops) *flops = ctx->c.flops;
+  if (flops) *flops = ctx->c.flops + ctx->c.flops32;
   return TT_OK;
 }
 
@@ -173,6 +173,7 @@ int tt_ctx_reset_counters(tt_ctx *ctx) {
   if (!ctx) return TT_EINVAL;
   ctx->c.launches = 0;
   ctx->c.flops = 0.0;
+  ctx->c.flops32 = 0.0;
   return TT_OK;
 }
 
@@ -180,9 +181,9 @@ int tt_ctx_set_profiling(tt_ctx *ctx, int on) {
   return guarded(ctx, [&] {
     ctx->c.prof_fold();
     ctx->c.profiling = on != 0;
-    ctx->c.gemm_flops = ctx->c.gemm32_flops = ctx->c.gemmtc_flops = 0.0;
-    ctx->c.gemm_launches = ctx->c.gemm32_launches = ctx->c.gemmtc_launches = 0;
-    ctx->c.gemm_ms_done = ctx->c.gemm32_ms_done = ctx->c.gemmtc_ms_done = 0.0;
+    ctx->c.gemm_flops = ctx->c.gemm32_flops = ctx->c.gemmtc_flops = ctx->c.pg_flops = 0.0;
+    ctx->c.gemm_launches = ctx->c.gemm32_launches = ctx->c.gemmtc_launches = ctx->c.pg_launches = 0;
+    ctx->c.gemm_ms_done = ctx->c.gemm32_ms_done = ctx->c.gemmtc_ms_done = ctx->c.pg_ms_done = 0.0;
   });
 }
 
@@ -192,6 +193,15 @@ int tt_ctx_gemm_stats(tt_ctx *ctx, int64_t *launches, double *ms, double *flops)
     if (launches) *launches = ctx->c.gemm_launches;
     if (ms) *ms = ctx->c.gemm_ms_done;
     if (flops) *flops = ctx->c.gemm_flops;
+  });
+}
+
+int tt_ctx_gmres_stats(tt_ctx *ctx, int64_t *launches, double *ms, double *flops) {
+  return guarded(ctx, [&] {
+    ctx->c.prof_fold();
+    if (launches) *launches = ctx->c.pg_launches;
+    if (ms) *ms = ctx->c.pg_ms_done;
+    if (flops) *flops = ctx->c.pg_flops;
   });
 }
 

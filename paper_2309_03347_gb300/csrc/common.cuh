@@ -96,9 +96,9 @@ struct Ctx {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
   size_t ev_used = 0;
   std::vector<int> ev_tag;  // 0: FP64 GEMM, 1: FP32 GEMM, 2: tcgen05 TF32 GEMM
-  double gemm_flops = 0.0, gemm32_flops = 0.0, gemmtc_flops = 0.0;
-  int64_t gemm_launches = 0, gemm32_launches = 0, gemmtc_launches = 0;
-  double gemm_ms_done = 0.0, gemm32_ms_done = 0.0, gemmtc_ms_done = 0.0;  // folded-in event times
+  double gemm_flops = 0.0, gemm32_flops = 0.0, gemmtc_flops = 0.0, pg_flops = 0.0;
+  int64_t gemm_launches = 0, gemm32_launches = 0, gemmtc_launches = 0, pg_launches = 0;
+  double gemm_ms_done = 0.0, gemm32_ms_done = 0.0, gemmtc_ms_done = 0.0, pg_ms_done = 0.0;  // folded-in event times
   DBuf ws_tc;  // split-K partial sums of the tensor-core GEMM
   void prof_begin(cudaEvent_t *b, cudaEvent_t *e, int tag = 0);
   void prof_fold();

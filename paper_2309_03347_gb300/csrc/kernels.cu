@@ -69,7 +69,8 @@ void Ctx::prof_fold() {
   for (size_t i = 0; i < ev_used; ++i) {
     float ms = 0.f;
     TT_CHECK_CUDA(cudaEventElapsedTime(&ms, ev_pool[i].first, ev_pool[i].second));
-    (ev_tag[i] == 2 ? gemmtc_ms_done : ev_tag[i] == 1 ? gemm32_ms_done : gemm_ms_done) += ms;
+    (ev_tag[i] == 3 ? pg_ms_done : ev_tag[i] == 2 ? gemmtc_ms_done : ev_tag[i] == 1 ? gemm32_ms_done : gemm_ms_done) +=
+        ms;
   }
   ev_used = 0;
 }
@@ -182,6 +183,64 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, double 
   }
 }
 
+// Small-tile FP64 GEMM for products too small to fill the GPU with 64 x 64
+// tiles.  FP64 issues at about 2 FMA per clock per SM on this part, so a
+// GEMM's time is its FMA count divided by the SMs it reaches: 16 x 16 output
+// tiles (one output per thread) and a K split give every SM work.  K step
+// 16 with the next step's operands loaded into registers during the current
+// step's products.
+constexpr int SBM = 16, SBN = 16, SBK = 16;
+
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(256) dgemm16_kernel(int M, int N, int K, double alpha,
+                                                      const double *__restrict__ A, int lda, long long sA,
+                                                      const double *__restrict__ B, int ldb, long long sB,
+                                                      double beta, double *__restrict__ C, int ldc, long long sC,
+                                                      int splitk, int kchunk, double *__restrict__ ws) {
+  __shared__ double As[SBK][SBM + 1];
+  __shared__ double Bs[SBK][SBN + 1];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int bz = blockIdx.z, bb = bz / splitk, split = bz % splitk;
+  const int m0 = blockIdx.y * SBM, n0 = blockIdx.x * SBN;
+  const int kbeg = split * kchunk, kend = min(K, kbeg + kchunk);
+  A += bb * sA;
+  B += bb * sB;
+  // element loaded by this thread: A (row am, k ak), B (k bk, column bn)
+  const int am = TA ? (tid & 15) : (tid >> 4), ak = TA ? (tid >> 4) : (tid & 15);
+  const int bn = TB ? (tid >> 4) : (tid & 15), bk = TB ? (tid & 15) : (tid >> 4);
+  auto ldA = [&](int k0) {
+    const int gm = m0 + am, gk = k0 + ak;
+    return (gm < M && gk < kend) ? (TA ? A[(long long)gk * lda + gm] : A[(long long)gm * lda + gk]) : 0.0;
+  };
+  auto ldB = [&](int k0) {
+    const int gn = n0 + bn, gk = k0 + bk;
+    return (gn < N && gk < kend) ? (TB ? B[(long long)gn * ldb + gk] : B[(long long)gk * ldb + gn]) : 0.0;
+  };
+  double acc = 0.0;
+  double ra = kbeg < kend ? ldA(kbeg) : 0.0, rb = kbeg < kend ? ldB(kbeg) : 0.0;
+  for (int k0 = kbeg; k0 < kend; k0 += SBK) {
+    As[ak][am] = ra;
+    Bs[bk][bn] = rb;
+    __syncthreads();
+    if (k0 + SBK < kend) {
+      ra = ldA(k0 + SBK);
+      rb = ldB(k0 + SBK);
+    }
+#pragma unroll
+    for (int kk = 0; kk < SBK; ++kk) acc = fma(As[kk][ty], Bs[kk][tx], acc);
+    __syncthreads();
+  }
+  const int gm = m0 + ty, gn = n0 + tx;
+  if (gm < M && gn < N) {
+    if (splitk == 1) {
+      double *cp = C + bb * sC + (long long)gm * ldc + gn;
+      *cp = beta == 0.0 ? alpha * acc : alpha * acc + beta * *cp;
+    } else {
+      ws[(long long)bz * M * N + (long long)gm * N + gn] = acc;
+    }
+  }
+}
+
 __global__ void splitk_reduce(int M, int N, int splitk, int batch, const double *__restrict__ ws,
                               double alpha, double beta, double *__restrict__ C, int ldc, long long sC) {
   const long long tot = (long long)batch * M * N;
@@ -213,31 +272,43 @@ void gemm(Ctx *c, bool ta, bool tb, int M, int N, int K, double alpha, const dou
     return;
   }
   const long long tiles = (long long)((M + GBM - 1) / GBM) * ((N + GBN - 1) / GBN) * batch;
-  int splitk = 1;
   const long long target = 2LL * c->sm_count;
-  if (tiles < target && K > 4 * GBK) {
-    splitk = (int)std::min<long long>((target + tiles - 1) / tiles, (K + 63) / 64);
-    splitk = std::max(1, std::min(splitk, 64));
+  // too few 64 x 64 tiles to reach every SM: 16 x 16 tiles with a K split
+  const bool small = tiles < c->sm_count;
+  const int TM = small ? SBM : GBM, TN = small ? SBN : GBN, TK = small ? SBK : GBK;
+  const long long tl = (long long)((M + TM - 1) / TM) * ((N + TN - 1) / TN) * batch;
+  int splitk = 1;
+  if (small) {
+    if (tl < target && K > TK) splitk = (int)std::min<long long>((target + tl - 1) / tl, (K + TK - 1) / TK);
+  } else if (tl < target && K > 4 * TK) {
+    splitk = (int)std::min<long long>((target + tl - 1) / tl, (K + 63) / 64);
   }
+  splitk = std::max(1, std::min(splitk, 64));
   int kchunk = (K + splitk - 1) / splitk;
-  kchunk = (kchunk + GBK - 1) / GBK * GBK;
+  kchunk = (kchunk + TK - 1) / TK * TK;
   splitk = (K + kchunk - 1) / kchunk;
   TT_REQUIRE((long long)batch * splitk <= 65535, "gemm: batch too large");
-  TT_REQUIRE((M + GBM - 1) / GBM <= 65535, "gemm: M too large");
+  TT_REQUIRE((M + TM - 1) / TM <= 65535, "gemm: M too large");
   double *ws = nullptr;
   if (splitk > 1) {
     c->ws_gemm.ensure(c, (size_t)batch * splitk * M * N);
     ws = c->ws_gemm.p();
   }
-  dim3 grid((N + GBN - 1) / GBN, (M + GBM - 1) / GBM, batch * splitk);
+  dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM, batch * splitk);
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   if (c->profiling) {
     c->prof_begin(&ev0, &ev1);
     TT_CHECK_CUDA(cudaEventRecord(ev0, c->stream));
   }
-#define GEMM_LAUNCH(TA_, TB_)                                                                       \
-  dgemm_kernel<TA_, TB_><<<grid, 256, 0, c->stream>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, \
-                                                      C, ldc, sC, splitk, kchunk, ws)
+#define GEMM_LAUNCH(TA_, TB_)                                                                                   \
+  do {                                                                                                          \
+    if (small)                                                                                                  \
+      dgemm16_kernel<TA_, TB_><<<grid, 256, 0, c->stream>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, \
+                                                            sC, splitk, kchunk, ws);                            \
+    else                                                                                                        \
+      dgemm_kernel<TA_, TB_><<<grid, 256, 0, c->stream>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc,   \
+                                                          sC, splitk, kchunk, ws);                              \
+  } while (0)
   if (ta && tb) GEMM_LAUNCH(true, true);
   else if (ta) GEMM_LAUNCH(true, false);
   else if (tb) GEMM_LAUNCH(false, true);
@@ -893,14 +964,20 @@ void gemm_f32(Ctx *c, bool ta, bool tb, int M, int N, int K, float alpha, const 
               const float *B, int ldb, long long sB, float beta, float *C, int ldc, long long sC, int batch) {
   if (M <= 0 || N <= 0 || batch <= 0 || K <= 0) return;
   const long long tiles = (long long)((M + GBM - 1) / GBM) * ((N + GBN - 1) / GBN) * batch;
-  int splitk = 1;
   const long long target = 2LL * c->sm_count;
-  if (tiles < target && K > 4 * GBK) {
-    splitk = (int)std::min<long long>((target + tiles - 1) / tiles, (K + 63) / 64);
-    splitk = std::max(1, std::min(splitk, 64));
+  // too few 64 x 64 tiles to reach every SM: 16 x 16 tiles with a K split
+  const bool small = tiles < c->sm_count;
+  const int TM = small ? SBM : GBM, TN = small ? SBN : GBN, TK = small ? SBK : GBK;
+  const long long tl = (long long)((M + TM - 1) / TM) * ((N + TN - 1) / TN) * batch;
+  int splitk = 1;
+  if (small) {
+    if (tl < target && K > TK) splitk = (int)std::min<long long>((target + tl - 1) / tl, (K + TK - 1) / TK);
+  } else if (tl < target && K > 4 * TK) {
+    splitk = (int)std::min<long long>((target + tl - 1) / tl, (K + 63) / 64);
   }
+  splitk = std::max(1, std::min(splitk, 64));
   int kchunk = (K + splitk - 1) / splitk;
-  kchunk = (kchunk + GBK - 1) / GBK * GBK;
+  kchunk = (kchunk + TK - 1) / TK * TK;
   splitk = (K + kchunk - 1) / kchunk;
   TT_REQUIRE((long long)batch * splitk <= 65535, "gemm_f32: batch too large");
   float *ws = nullptr;
@@ -908,7 +985,7 @@ void gemm_f32(Ctx *c, bool ta, bool tb, int M, int N, int K, float alpha, const 
     c->ws_gemm32.ensure(c, ((size_t)batch * splitk * M * N + 1) / 2);
     ws = reinterpret_cast<float *>(c->ws_gemm32.p());
   }
-  dim3 grid((N + GBN - 1) / GBN, (M + GBM - 1) / GBM, batch * splitk);
+  dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM, batch * splitk);
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   if (c->profiling) {
     c->prof_begin(&ev0, &ev1, 1);

@@ -509,12 +509,29 @@ int pgmres32(Ctx *c, const float *PL, const float *A32, const float *PR, int r0,
   P.gv = gv;
   P.tol = tol;
   void *args[] = {&P};
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  if (c->profiling) {
+    c->prof_begin(&ev0, &ev1, 3);
+    TT_CHECK_CUDA(cudaEventRecord(ev0, c->stream));
+  }
   TT_CHECK_CUDA(cudaLaunchCooperativeKernel((const void *)pgmres_kernel, dim3(G), dim3(PG_THREADS), args, 0,
                                             c->stream));
   c->count();
+  if (c->profiling) TT_CHECK_CUDA(cudaEventRecord(ev1, c->stream));
   int hs[2];
   TT_CHECK_CUDA(cudaMemcpyAsync(hs, W.st.p(), 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   c->sync();
+  // algorithmic work: one local matvec per Arnoldi step plus the restart residuals
+  // (2 n r0 r1 (r0 R1 + n R1 R2 + r1 R2) each), and the two Gram-Schmidt passes
+  // (4 N flops per stored vector per pass, counted with the mean basis size)
+  const double mv = 2.0 * m * (double)r0 * r1 * ((double)r0 * R1 + (double)m * R1 * R2 + (double)r1 * R2);
+  const int steps = std::max(hs[0], 0);
+  const int cycles = (steps + restart - 1) / std::max(restart, 1);
+  c->flops32 += mv * (steps + std::max(cycles - 1, 0));
+  if (c->profiling) {
+    c->pg_launches += 1;
+    c->pg_flops += mv * (steps + std::max(cycles - 1, 0)) + 8.0 * N * steps * (0.5 * (std::min(steps, restart) + 1));
+  }
   if (hs[1] == TT_ETIMEOUT) throw Error(TT_ETIMEOUT, "pgmres32: grid barrier gave up waiting");
   if (hs[1] != 0) throw Error(TT_ENONFINITE, "pgmres32: non-finite Krylov vector");
   return hs[0];
