@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(PG_THREADS, 1) pgmres_kernel(PGArgs P) {
   __shared__ float As[TBK][TBM + 1];
   __shared__ float Bs[TBK][TBN + 1];
   __shared__ float wsh[PG_CHUNK];
-  __shared__ double hsh[PG_MAXR + 1];  // Gram-Schmidt coefficients of the stored vectors
+  __shared__ float hsc[PG_MAXR + 1];   // Gram-Schmidt coefficients of the stored vectors
   __shared__ double ss[PG_MAXR + 1];   // scales s_v of the stored vectors (same in every CTA)
   __shared__ double red[PG_THREADS / 32];
   // Arnoldi state, used by CTA 0 only
@@ -249,36 +249,38 @@ __global__ void __launch_bounds__(PG_THREADS, 1) pgmres_kernel(PGArgs P) {
     for (int b = lane; b < Gv; b += 32) a += __ldcg(part + (size_t)v * Gv + b);
     return warp_sum_d(a);
   };
-  // w_i - sum_{v <= j} V_v[i] c_v for the slice (c in hsh), four loads in flight
+  // sum_{v <= j} V_v[i] c_v for the slice (c in hsc, FP32 products and sums:
+  // the Krylov vectors are FP32), eight loads in flight
   auto sub_comb = [&](int i, int j) {
     const float *base = P.V + lo + i;
-    double a[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    float a[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     int v = 0;
     for (; v + 7 <= j; v += 8) {
       float xv[8];
 #pragma unroll
       for (int u = 0; u < 8; ++u) xv[u] = __ldcg(base + (size_t)(v + u) * N);
 #pragma unroll
-      for (int u = 0; u < 8; ++u) a[u] = fma((double)xv[u], hsh[v + u], a[u]);
+      for (int u = 0; u < 8; ++u) a[u] = fmaf(xv[u], hsc[v + u], a[u]);
     }
-    for (; v <= j; ++v) a[0] = fma((double)__ldcg(base + (size_t)v * N), hsh[v], a[0]);
+    for (; v <= j; ++v) a[0] = fmaf(__ldcg(base + (size_t)v * N), hsc[v], a[0]);
     return ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
   };
-  // partial inner products of the slice of w (in wsh) with the stored vectors v <= j
+  // partial inner products of the slice of w (in wsh) with the stored vectors
+  // v <= j: FP32 products summed per lane, FP64 across lanes and CTAs
   auto inner = [&](double *part, int j) {
     for (int v = warp; v <= j; v += nwarp) {
       const float *vv = P.V + (size_t)v * N + lo;
-      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+      float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
       int i = lane;
       for (; i + 96 < cn; i += 128) {
         const float x0 = __ldcg(vv + i), x1 = __ldcg(vv + i + 32), x2 = __ldcg(vv + i + 64), x3 = __ldcg(vv + i + 96);
-        a0 = fma((double)x0, (double)wsh[i], a0);
-        a1 = fma((double)x1, (double)wsh[i + 32], a1);
-        a2 = fma((double)x2, (double)wsh[i + 64], a2);
-        a3 = fma((double)x3, (double)wsh[i + 96], a3);
+        a0 = fmaf(x0, wsh[i], a0);
+        a1 = fmaf(x1, wsh[i + 32], a1);
+        a2 = fmaf(x2, wsh[i + 64], a2);
+        a3 = fmaf(x3, wsh[i + 96], a3);
       }
-      for (; i < cn; i += 32) a0 = fma((double)__ldcg(vv + i), (double)wsh[i], a0);
-      double a = warp_sum_d((a0 + a1) + (a2 + a3));
+      for (; i < cn; i += 32) a0 = fmaf(__ldcg(vv + i), wsh[i], a0);
+      const double a = warp_sum_d((double)a0 + (double)a1 + ((double)a2 + (double)a3));
       if (lane == 0 && bid < Gv) part[(size_t)v * Gv + bid] = a * ss[v];
     }
   };
@@ -406,17 +408,18 @@ __global__ void __launch_bounds__(PG_THREADS, 1) pgmres_kernel(PGArgs P) {
         for (int v = warp; v <= j; v += nwarp) {
           const double h = warp_part_sum(part, v);
           if (lane == 0) {
-            hsh[v] = h * ss[v];
+            hsc[v] = (float)(h * ss[v]);
             if (bid == 0) (pass == 0 ? sh1 : sh2)[v] = h;
           }
         }
         __syncthreads();
-        double sq = 0.0;
+        float sqf = 0.f;
         for (int i = tid; i < cn; i += PG_THREADS) {
-          const float nw = (float)((double)wsh[i] - sub_comb(i, j));
+          const float nw = wsh[i] - sub_comb(i, j);
           wsh[i] = nw;
-          sq = fma((double)nw, (double)nw, sq);
+          sqf = fmaf(nw, nw, sqf);
         }
+        double sq = (double)sqf;
         __syncthreads();
         if (pass == 0) {
           inner(D + L.part2, j);
@@ -441,9 +444,9 @@ __global__ void __launch_bounds__(PG_THREADS, 1) pgmres_kernel(PGArgs P) {
       for (int i = 0; i < kk; ++i) y[i] *= ss[i];
     }
     if (!grid_sync(P.bar, err)) return;
-    for (int v = tid; v <= jend; v += PG_THREADS) hsh[v] = -__ldcg(D + L.y + v);
+    for (int v = tid; v <= jend; v += PG_THREADS) hsc[v] = (float)__ldcg(D + L.y + v);
     __syncthreads();
-    for (int i = tid; i < cn; i += PG_THREADS) P.x[lo + i] = (float)((double)P.x[lo + i] - sub_comb(i, jend));
+    for (int i = tid; i < cn; i += PG_THREADS) P.x[lo + i] += sub_comb(i, jend);
     if (!grid_sync(P.bar, err)) return;
     if (__ldcg(P.st + 3)) break;
   }

@@ -34,12 +34,6 @@ namespace {
 constexpr int J32_THREADS = 1024;
 constexpr int J32_MAX_SWEEPS = 12;
 
-__device__ __forceinline__ float warp_sum_f(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
 // B (n x n, column-major, FP64 input) -> V (n x n column-major FP32 rotations)
 __global__ void __launch_bounds__(J32_THREADS) jacobi32_kernel(const double *__restrict__ Bin, int n,
                                                                float *__restrict__ Vout) {
@@ -75,12 +69,17 @@ __global__ void __launch_bounds__(J32_THREADS) jacobi32_kernel(const double *__r
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   const int np = (n + 1) & ~1;
   const float tol = fmaxf(2e-6f, 1.2e-7f * sqrtf((float)n));
+  // a group of 8 lanes per column pair (4 pairs per warp): vectors of a few
+  // dozen entries leave a full warp mostly idle, and a round's cost is its
+  // instruction count
+  const int sl = lane & 7;
   for (int sweep = 0; sweep < J32_MAX_SWEEPS; ++sweep) {
     if (threadIdx.x == 0) s_rot = 0;
     __syncthreads();
     for (int round = 0; round < np - 1; ++round) {
-      for (int t = warp; t < np / 2; t += nwarp) {
-        int p, q;
+      for (int t0 = warp * 4; t0 < np / 2; t0 += nwarp * 4) {
+        const int t = t0 + (lane >> 3);
+        int p = 0, q = 0;
         if (t == 0) {
           p = np - 1;
           q = round;
@@ -88,26 +87,30 @@ __global__ void __launch_bounds__(J32_THREADS) jacobi32_kernel(const double *__r
           p = (round + t) % (np - 1);
           q = (round - t + (np - 1)) % (np - 1);
         }
-        if (p >= n || q >= n) continue;
+        const bool valid = t < np / 2 && p < n && q < n;
         float *bp = B + (long long)p * n, *bq = B + (long long)q * n;
         float al = 0.f, be = 0.f, ga = 0.f;
-        for (int i = lane; i < n; i += 32) {
-          const float x = bp[i], y = bq[i];
-          al = fmaf(x, x, al);
-          be = fmaf(y, y, be);
-          ga = fmaf(x, y, ga);
+        if (valid)
+          for (int i = sl; i < n; i += 8) {
+            const float x = bp[i], y = bq[i];
+            al = fmaf(x, x, al);
+            be = fmaf(y, y, be);
+            ga = fmaf(x, y, ga);
+          }
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, o);
+          be += __shfl_xor_sync(0xffffffffu, be, o);
+          ga += __shfl_xor_sync(0xffffffffu, ga, o);
         }
-        al = warp_sum_f(al);
-        be = warp_sum_f(be);
-        ga = warp_sum_f(ga);
-        if (ga == 0.f || al == 0.f || be == 0.f) continue;
+        if (!valid || ga == 0.f || al == 0.f || be == 0.f) continue;
         if (fabsf(ga) <= tol * sqrtf(al * be)) continue;
         const float zeta = (be - al) / (2.f * ga);
         const float tt = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
         const float cs = 1.f / sqrtf(1.f + tt * tt);
         const float sn = cs * tt;
         float *vp = V + (long long)p * n, *vq = V + (long long)q * n;
-        for (int i = lane; i < n; i += 32) {
+        for (int i = sl; i < n; i += 8) {
           const float x = bp[i], y = bq[i];
           bp[i] = cs * x - sn * y;
           bq[i] = sn * x + cs * y;
@@ -115,7 +118,7 @@ __global__ void __launch_bounds__(J32_THREADS) jacobi32_kernel(const double *__r
           vp[i] = cs * u - sn * w;
           vq[i] = sn * u + cs * w;
         }
-        if (lane == 0) atomicAdd(&s_rot, 1);
+        if (sl == 0) atomicAdd(&s_rot, 1);
       }
       __syncthreads();
     }
