@@ -581,7 +581,7 @@ constexpr int QR_THREADS = 512;
 __global__ void __launch_bounds__(QR_THREADS) householder_qr_kernel(double *__restrict__ A, int m, int n,
                                                                     double *__restrict__ tau,
                                                                     double *__restrict__ Q,
-                                                                    double *__restrict__ R) {
+                                                                    double *__restrict__ R, int form_q) {
   __shared__ double sh[32];
   __shared__ double s_beta, s_tau, s_scale;
   const int k = min(m, n);
@@ -634,6 +634,7 @@ __global__ void __launch_bounds__(QR_THREADS) householder_qr_kernel(double *__re
     const int r = (int)(e % k), cc = (int)(e / k);
     R[e] = (r <= cc) ? A[(long long)cc * m + r] : 0.0;
   }
+  if (!form_q) return;
   // Q (m x k) = H_0 ... H_{k-1} I
   for (long long e = threadIdx.x; e < (long long)m * k; e += blockDim.x) {
     const int r = (int)(e % m), cc = (int)(e / m);
@@ -658,12 +659,64 @@ __global__ void __launch_bounds__(QR_THREADS) householder_qr_kernel(double *__re
   }
 }
 
+// V (m x k, column-major): the Householder vectors left below the diagonal of
+// A with the implicit unit diagonal; a reflector with tau = 0 (H = I) gets v = 0.
+__global__ void wy_v_kernel(const double *__restrict__ A, const double *__restrict__ tau, int m, int k,
+                            double *__restrict__ V) {
+  const long long tot = (long long)m * k;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e % m), j = (int)(e / m);
+    V[e] = tau[j] == 0.0 ? 0.0 : (i < j ? 0.0 : (i == j ? 1.0 : A[e]));
+  }
+}
+
+// X = S^-1 V1^T with S = strictly-upper(W) + diag(1/tau) (W = V^T V, row-major
+// k x k) and V1 the top k x k block of V: one thread per column of X, back
+// substitution (X row-major k x k).  H_0 ... H_{k-1} = I - V S^-1 V^T (the UT
+// form of a product of Householder reflectors).
+__global__ void ut_solve_kernel(const double *__restrict__ W, const double *__restrict__ tau,
+                                const double *__restrict__ V, int m, int k, double *__restrict__ X) {
+  const int cc = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cc >= k) return;
+  for (int i = k - 1; i >= 0; --i) {
+    double acc = V[cc + (long long)i * m];  // V1^T[i][cc] = V1[cc][i]
+    for (int l = i + 1; l < k; ++l) acc -= W[(long long)i * k + l] * X[(long long)l * k + cc];
+    const double t = tau[i];
+    X[(long long)i * k + cc] = t == 0.0 ? 0.0 : acc * t;
+  }
+}
+
+__global__ void eye_kernel(double *__restrict__ Q, int m, int k) {
+  const long long tot = (long long)m * k;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x)
+    Q[e] = (e % m) == (e / m) ? 1.0 : 0.0;
+}
+
 void qr_colmajor(Ctx *c, double *A, int m, int n, double *Q, double *R) {
   TT_REQUIRE(m > 0 && n > 0, "qr: empty matrix");
   const int k = std::min(m, n);
   c->scratch[6].ensure(c, (size_t)k);
-  householder_qr_kernel<<<1, QR_THREADS, 0, c->stream>>>(A, m, n, c->scratch[6].p(), Q, R);
+  double *tau = c->scratch[6].p();
+  // Q from the UT form with multi-SM FP64 products for 8 <= k <= 128; the
+  // one-CTA backward accumulation otherwise
+  const bool ut = k >= 8 && k <= 128;
+  householder_qr_kernel<<<1, QR_THREADS, 0, c->stream>>>(A, m, n, tau, Q, R, ut ? 0 : 1);
   LAUNCH_CHECK(c);
+  if (!ut) return;
+  const size_t mk = (size_t)m * k, kk = (size_t)k * k;
+  DBuf V(c, mk), W(c, kk), X(c, kk);
+  wy_v_kernel<<<ew_blocks(c, mk), 256, 0, c->stream>>>(A, tau, m, k, V.p());
+  LAUNCH_CHECK(c);
+  // W = V^T V (V column-major m x k is row-major V^T, ld m)
+  gemm(c, false, true, k, k, m, 1.0, V.p(), m, 0, V.p(), m, 0, 0.0, W.p(), k, 0);
+  ut_solve_kernel<<<(k + 63) / 64, 64, 0, c->stream>>>(W.p(), tau, V.p(), m, k, X.p());
+  LAUNCH_CHECK(c);
+  // Q = I - V X: Q column-major is row-major Q^T (k x m, ld m); Q^T -= X^T V^T
+  eye_kernel<<<ew_blocks(c, mk), 256, 0, c->stream>>>(Q, m, k);
+  LAUNCH_CHECK(c);
+  gemm(c, true, false, k, m, k, -1.0, X.p(), k, 0, V.p(), m, 0, 1.0, Q, m, 0);
 }
 
 // ----------------------------------------------------------------- Jacobi SVD
