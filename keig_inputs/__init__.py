@@ -318,3 +318,24 @@ def random_cores(modes, ranks, seed: int) -> List[np.ndarray]:
     rng = np.random.default_rng(seed)
     return [rng.standard_normal((ranks[k], modes[k], ranks[k + 1]))
             for k in range(len(modes))]
+
+
+def fissile_response(prob: Problem, group: int = 0):
+    """Weights of the flux functional J = sum over fissile cells of
+    vol * (8-corner average of the group-``group`` scalar flux), written as
+    J = sum_g sum_v resp_g[g] resp_v[v] phi[g, v] on the vertices.
+
+    resp_g is the unit vector of ``group``; resp_v[v] adds vol / 8 for every
+    fissile cell (nu_sig_f > 0 in some group) that has v as a corner, in the
+    vertex order of the scalar flux (z, y, x; x fastest)."""
+    n = prob.n
+    fissile = (prob.nu_sig_f.max(axis=1) > 0)[prob.mat]  # (cz, cy, cx)
+    vol = float(np.prod(prob.delta))
+    resp_v = np.zeros((n, n, n))
+    for a in (0, 1):
+        for b in (0, 1):
+            for c in (0, 1):
+                resp_v[a:a + n - 1, b:b + n - 1, c:c + n - 1] += fissile * (vol / 8.0)
+    resp_g = np.zeros(prob.G)
+    resp_g[group] = 1.0
+    return resp_g, resp_v

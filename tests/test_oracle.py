@@ -244,3 +244,23 @@ def test_finite_difference_gradients_match_dense_adjoint():
     scale = max(np.abs(v).max() for v in ad.values())
     for f in SE.FIELDS:
         assert np.abs(fd[f] - ad[f]).max() < 1e-6 * scale, f
+
+
+def test_functional_gradients_gpt_match_finite_differences():
+    # the flux functional J (fissile-region group-1 flux of the
+    # production-normalised eigenvector): central differences of the oracle's
+    # J against generalised perturbation theory with the dense operators
+    from oracle import sensitivity as SE
+    import dataclasses
+    p = dataclasses.replace(ki.fissile_box(l=2, G=2, order=4, seed=1003, half_width=1), side=(2.0,) * 3)
+    rg, rv = ki.fissile_response(p, 0)
+    fd = SE.fd_functional_gradients(p, rg, rv)
+    gp, J, k = SE.dense_gpt_gradients(p, rg, rv)
+    j_or, k_or = SE.oracle_functional(p, rg, rv)
+    assert abs(J - j_or) < 1e-10 * abs(J) and abs(k - k_or) < 1e-10 * k
+    scale = max(np.abs(v).max() for v in gp.values())
+    for f in SE.FIELDS:
+        assert np.abs(fd[f] - gp[f]).max() < 1e-7 * scale, f
+    # the normalisation term matters: without -J sum(dF Psi) the fission
+    # derivatives would be wrong
+    assert np.abs(gp["nu_sig_f"]).max() > 1e-3 * scale
