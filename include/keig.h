@@ -320,6 +320,38 @@ typedef struct {
 int keig_sensitivities(tt_ctx *ctx, const tt_problem *prob, const keig_opts *opts, double *dk_dsig_t,
                        double *dk_dsig_s, double *dk_dnu_sig_f, double *dk_dchi, keig_sens_info *info);
 
+/* Gradient of a flux functional by generalised perturbation theory (GPT).
+ * The functional is J = sum_g sum_v resp_g[g] resp_v[v] phi[g, v] of the
+ * scalar flux phi = sum_l w_l Psi[g, l, v] of the eigenvector normalised so
+ * that sum(F Psi) = <f, Psi> = 1 (f = F^T 1).  With A = H - S - F/k,
+ * differentiating A Psi = 0, the normalisation and J, and introducing the
+ * generalised adjoint Gamma with
+ *   A^T Gamma = j - J f,   <Gamma, F Psi> = 0     (j = resp_g (x) w (x) resp_v),
+ * gives  dJ/dp = -<Gamma, (dH/dp - dS/dp - (dF/dp)/k) Psi> - J sum((dF/dp) Psi).
+ * The paper has no adjoint; this follows from Eq. (OpFormkNTE).  Gamma comes
+ * from the fixed-source iteration H^T Gamma' = (S^T + F^T/k) Gamma + (j - J f)
+ * on the transposed TT operators (AMEn product and solve as in the k fixed
+ * point), with the fundamental adjoint mode removed after every step
+ * (Gamma' -= <Gamma', F Psi> / <Psi^dagger, F Psi> Psi^dagger); it converges at
+ * the dominance ratio.  The derivatives then use the same per-material open
+ * contractions as keig_sensitivities.
+ * resp_g: [G] host; resp_v: [(2^l)^3] host, vertex order z, y, x (x fastest),
+ * the order of phi_out of keig_fixed_point; the angular weights are those of
+ * prob (octant-symmetric: phi = sum over octants and prob->w).  tol_gpt: stop when the relative
+ * change of Gamma falls below it; max_gpt: step limit (1..10000).
+ * Outputs as keig_sensitivities (dJ instead of dk).  TT_ENOCONV if a fixed
+ * point or the GPT iteration reached its limit (outputs still written). */
+typedef struct {
+  double J;               /* the functional of the production-normalised eigenvector */
+  double k;               /* forward eigenvalue */
+  int iters, iters_adjoint, iters_gpt;
+  double gpt_change;      /* relative change of Gamma at the last GPT step */
+  double wall_ms;
+} keig_gpt_info;
+int keig_gpt(tt_ctx *ctx, const tt_problem *prob, const keig_opts *opts, const double *resp_g,
+             const double *resp_v, double tol_gpt, int max_gpt, double *dJ_dsig_t, double *dJ_dsig_s,
+             double *dJ_dnu_sig_f, double *dJ_dchi, keig_gpt_info *info);
+
 /* Scalar flux of a flux TT (contract the octant and direction cores with the
  * quadrature weights, Appendix B.4) as a TT with cores [G][2 x 3l]. */
 int tt_scalar_flux(tt_ctx *ctx, const tt_vec *psi, const double *w_host, int n_dir, tt_vec **phi);

@@ -506,6 +506,40 @@ def keig_sensitivities(ctx: Context, prob, opts: Optional[KeigOpts] = None, allo
                 wall_ms=info.wall_ms, code=rc)
 
 
+class KeigGptInfo(C.Structure):
+    _fields_ = [("J", C.c_double), ("k", C.c_double), ("iters", C.c_int), ("iters_adjoint", C.c_int),
+                ("iters_gpt", C.c_int), ("gpt_change", C.c_double), ("wall_ms", C.c_double)]
+
+
+def keig_gpt(ctx: Context, prob, resp_g, resp_v, opts: Optional[KeigOpts] = None, tol_gpt: float = 1e-8,
+             max_gpt: int = 500, allow_noconv: bool = False):
+    """dJ/d(table entry) of the flux functional J = sum resp_g[g] resp_v[v]
+    phi[g, v] by generalised perturbation theory (keig.h: keig_gpt); returns
+    dict of arrays shaped like the tables plus J and the run information."""
+    lib = load()
+    if not getattr(lib.keig_gpt, "_marshalled", False):
+        lib.keig_gpt.argtypes = [C.c_void_p, C.POINTER(TTProblem), C.POINTER(KeigOpts), D, D, C.c_double, C.c_int,
+                                 D, D, D, D, C.POINTER(KeigGptInfo)]
+        lib.keig_gpt.restype = C.c_int
+        lib.keig_gpt._marshalled = True
+    pa = _ProblemArrays(prob)
+    o = opts if opts is not None else keig_default_opts()
+    nm, G = prob.n_mat, prob.G
+    rg = np.ascontiguousarray(resp_g, dtype=np.float64).ravel()
+    rv = np.ascontiguousarray(resp_v, dtype=np.float64).ravel()
+    if rg.size != G or rv.size != prob.n ** 3:
+        raise KeigError(TT_EINVAL, "keig_gpt: response sizes must be G and (2^l)^3")
+    gt, gs, gn, gc = np.zeros((nm, G)), np.zeros((nm, G, G)), np.zeros((nm, G)), np.zeros((nm, G))
+    info = KeigGptInfo()
+    rc = lib.keig_gpt(ctx.h, C.byref(pa.s), C.byref(o), _dp(rg), _dp(rv), float(tol_gpt), int(max_gpt), _dp(gt),
+                      _dp(gs), _dp(gn), _dp(gc), C.byref(info))
+    if not (allow_noconv and rc == TT_ENOCONV):
+        ctx.check(rc)
+    return dict(sig_t=gt, sig_s=gs, nu_sig_f=gn, chi=gc, J=info.J, k=info.k, iters=info.iters,
+                iters_adjoint=info.iters_adjoint, iters_gpt=info.iters_gpt, gpt_change=info.gpt_change,
+                wall_ms=info.wall_ms, code=rc)
+
+
 def keig_batch(problems, opts_list, n_workers: int = 8, contexts=None):
     """Solve independent problems side by side (keig.h: keig_batch).  One
     context per worker, each on its own torch CUDA stream.  Returns a list of

@@ -782,6 +782,157 @@ int keig_sensitivities(tt_ctx *ctx, const tt_problem *prob, const keig_opts *opt
   return rc;
 }
 
+int keig_gpt(tt_ctx *ctx, const tt_problem *prob, const keig_opts *opts, const double *resp_g,
+             const double *resp_v, double tol_gpt, int max_gpt, double *dJ_dsig_t, double *dJ_dsig_s,
+             double *dJ_dnu_sig_f, double *dJ_dchi, keig_gpt_info *info) {
+  int conv = 0;
+  const char *stage = "setup";
+  int rc = guarded(ctx, [&] {
+   try {
+    validate_problem(prob);
+    check_opts(opts);
+    TT_REQUIRE(resp_g && resp_v, "keig_gpt: null response");
+    TT_REQUIRE(dJ_dsig_t && dJ_dsig_s && dJ_dnu_sig_f && dJ_dchi, "keig_gpt: null output");
+    TT_REQUIRE(tol_gpt > 0 && max_gpt >= 1 && max_gpt <= 10000, "keig_gpt: bad tolerance or step limit");
+    const int G = prob->G, nm = prob->n_mat, l = prob->l;
+    const size_t nv = (size_t)1 << (3 * l);
+    check_finite_host(resp_g, G, "resp_g");
+    check_finite_host(resp_v, nv, "resp_v");
+    const auto t0 = clk::now();
+    tt::Ctx *c = &ctx->c;
+    tt::OpFactors fac = tt::make_factors(c, prob);
+    tt::TT H = tt::assemble_operator(c, prob, fac, TT_OP_H, -1, opts->eps_op);
+    tt::TT S = tt::assemble_operator(c, prob, fac, TT_OP_S, -1, opts->eps_op);
+    tt::TT F = tt::assemble_operator(c, prob, fac, TT_OP_F, -1, opts->eps_op);
+    tt::TT HT = tt::transpose_op(c, H), ST = tt::transpose_op(c, S), FT = tt::transpose_op(c, F);
+    tt::TTOp Fop;
+    Fop.t = tt::tt_clone(c, F);
+    KeigOps opsT = make_ops(c, tt::tt_clone(c, HT), tt::tt_clone(c, ST), tt::tt_clone(c, FT), opts);
+    KeigOps ops = make_ops(c, std::move(H), std::move(S), std::move(F), opts);
+    keig_result fwd, adj;
+    memset(&fwd, 0, sizeof(fwd));
+    memset(&adj, 0, sizeof(adj));
+    tt::TT psi, psa;
+    stage = "fixed points";
+    const bool c1 = run_fixed_point(c, ops, opts, &fwd, psi, t0, 0);
+    const bool c2 = run_fixed_point(c, opsT, opts, &adj, psa, t0, 77);
+    const double k = fwd.k;
+    const double P = bilinear(c, Fop, psa, psi);  // <Psi^dagger, F Psi>
+    TT_REQUIRE(std::isfinite(P) && P != 0.0, "keig_gpt: <Psi^dagger, F Psi> vanished");
+    stage = "F Psi";
+    tt::TT Fpsi = tt::matvec_exact(c, Fop.t, psi);
+    tt::round(c, Fpsi, 1e-13, 0);
+    // j = resp_g (x) (1_8 (x) w) (x) resp_v as a TT with the core order of Psi:
+    // the quadrature is octant-symmetric (w holds one octant's weights), so
+    // the angular factor has rank one; the vertex field is TT-SVD compressed
+    stage = "response TT";
+    tt::TT j;
+    {
+      const int npo = prob->n_dir;
+      tt::DBuf dv(c, nv);
+      TT_CHECK_CUDA(cudaMemcpyAsync(dv.p(), resp_v, nv * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+      tt::TT jv = tt::tt_svd_dense(c, dv.p(), std::vector<int>(3 * l, 2), 1e-15, 0);
+      j.d = 3 + jv.d;
+      j.n = {G, 8, npo};
+      j.r = {1, 1, 1};
+      j.core.resize(j.d);
+      j.core[0].alloc(c, (size_t)G);
+      j.core[1].alloc(c, 8);
+      j.core[2].alloc(c, (size_t)npo);
+      TT_CHECK_CUDA(cudaMemcpyAsync(j.core[0].p(), resp_g, (size_t)G * sizeof(double), cudaMemcpyHostToDevice,
+                                    c->stream));
+      tt::fill(c, j.core[1].p(), 8, 1.0);
+      TT_CHECK_CUDA(cudaMemcpyAsync(j.core[2].p(), prob->w, (size_t)npo * sizeof(double), cudaMemcpyHostToDevice,
+                                    c->stream));
+      for (int i = 0; i < jv.d; ++i) {
+        j.n.push_back(jv.n[i]);
+        j.r.push_back(jv.r[i]);
+        j.core[3 + i] = std::move(jv.core[i]);
+      }
+      j.r.push_back(1);
+      c->sync();  // the host staging above must outlive its copies
+    }
+    TT_REQUIRE(j.d == psi.d, "keig_gpt: response layout does not match the flux");
+    stage = "functional and GPT source";
+    const double J = tt::dot(c, j, psi);
+    // s = j - J f
+    tt::TT src = tt::add(c, 1.0, j, -J, ops.f);
+    tt::round(c, src, 1e-14, 0);
+    // H^T Gamma' = (S^T + F^T/k) Gamma + s, fundamental adjoint mode removed
+    tt::TTOp LT, RT;
+    LT.t = std::move(HT);
+    RT.t = tt::add(c, 1.0, ST, 1.0 / k, FT);
+    tt::TT gam = tt::tt_clone(c, src), B = tt::tt_clone(c, src);
+    double change = 1e300;
+    int it = 0;
+    bool c3 = false;
+    stage = "GPT iteration";
+    for (it = 0; it < max_gpt; ++it) {
+      tt::SolveStats mst, sst;
+      tt::amen_mv(c, RT, gam, B, opts->eps, opts->rmax, opts->mv_sweeps, opts->kick, 9000 + it, &mst);
+      tt::TT rhs = tt::add(c, 1.0, B, 1.0, src);
+      tt::round(c, rhs, opts->eps, opts->rmax);
+      tt::TT gnew = tt::tt_clone(c, gam);
+      tt::amen_solve(c, LT, rhs, gnew, opts->eps, opts->rmax, opts->solve_sweeps, opts->kick, 19000 + it, &sst,
+                     (int)opts->prec);
+      const double cdef = tt::dot(c, gnew, Fpsi) / P;
+      tt::TT g2 = tt::add(c, 1.0, gnew, -cdef, psa);
+      tt::round(c, g2, opts->eps, opts->rmax);
+      const double aa = tt::dot(c, g2, g2), bb = tt::dot(c, gam, gam), ab = tt::dot(c, g2, gam);
+      if (!std::isfinite(aa) || !std::isfinite(ab)) throw tt::Error(TT_ENONFINITE, "keig_gpt: non-finite adjoint");
+      change = std::sqrt(std::max(aa + bb - 2 * ab, 0.0) / std::max(aa, 1e-300));
+      gam = std::move(g2);
+      if (change < tol_gpt) {
+        ++it;
+        c3 = true;
+        break;
+      }
+    }
+    conv = c1 && c2 && c3;
+    // dJ/dp = -<Gamma, (dH - dS - dF/k) Psi> - J sum(dF Psi), per material through
+    // the open contractions (the sum is the contraction with the all-ones TT)
+    stage = "derivative contractions";
+    tt::TT ones = tt::tt_ones(c, psi.n);
+    for (int m = 0; m < nm; ++m) {
+      tt::TTOp Bc, Bs;
+      Bc.t = tt::assemble_operator(c, prob, fac, tt::KIND_COLLISION, m, opts->eps_op);
+      Bs.t = tt::assemble_operator(c, prob, fac, tt::KIND_SOURCE, m, opts->eps_op);
+      const std::vector<double> Wc = open_bilinear(c, Bc, gam, psi);
+      const std::vector<double> Ws = open_bilinear(c, Bs, gam, psi);
+      const std::vector<double> W1 = open_bilinear(c, Bs, ones, psi);
+      const double *chi = prob->chi + (size_t)m * G, *nsf = prob->nu_sig_f + (size_t)m * G;
+      for (int g = 0; g < G; ++g) {
+        dJ_dsig_t[(size_t)m * G + g] = -Wc[(size_t)g * G + g];
+        double a = 0.0, b = 0.0;
+        for (int h = 0; h < G; ++h) {
+          dJ_dsig_s[((size_t)m * G + g) * G + h] = Ws[(size_t)g * G + h];
+          a += chi[h] * (Ws[(size_t)h * G + g] / k - J * W1[(size_t)h * G + g]);  // d/d nsf_g
+          b += (Ws[(size_t)g * G + h] / k - J * W1[(size_t)g * G + h]) * nsf[h];  // d/d chi_g
+        }
+        dJ_dnu_sig_f[(size_t)m * G + g] = a;
+        dJ_dchi[(size_t)m * G + g] = b;
+      }
+    }
+    if (info) {
+      info->J = J;
+      info->k = k;
+      info->iters = fwd.iters;
+      info->iters_adjoint = adj.iters;
+      info->iters_gpt = it;
+      info->gpt_change = change;
+      info->wall_ms = std::chrono::duration<double, std::milli>(clk::now() - t0).count();
+    }
+   } catch (const tt::Error &e) {
+    throw tt::Error(e.code, std::string("keig_gpt (") + stage + "): " + e.what());
+   }
+  });
+  if (rc == TT_OK && !conv) {
+    ctx->c.err = "keig_gpt: a fixed point or the GPT iteration reached its limit";
+    return TT_ENOCONV;
+  }
+  return rc;
+}
+
 int keig_alpha(tt_ctx *ctx, const tt_problem *prob, const keig_opts *opts, double tol_k1, int max_steps,
                keig_alpha_result *out) {
   int conv = 0;

@@ -120,7 +120,8 @@ static void small_svd(Ctx *c, double *R, int k, double *U, double *S, double *V,
 }
 
 void svd_rm(Ctx *c, const double *A, int m, int n, SVD &o, int orth) {
-  TT_REQUIRE(m > 0 && n > 0, "svd: empty matrix");
+  if (m <= 0 || n <= 0)
+    throw Error(TT_EINVAL, "svd: empty matrix (" + std::to_string(m) + " x " + std::to_string(n) + ")");
   o.m = m;
   o.n = n;
   const int k = std::min(m, n);
