@@ -320,6 +320,36 @@ typedef struct {
 int keig_sensitivities(tt_ctx *ctx, const tt_problem *prob, const keig_opts *opts, double *dk_dsig_t,
                        double *dk_dsig_s, double *dk_dnu_sig_f, double *dk_dchi, keig_sens_info *info);
 
+/* ---------------------------------------------------------------- 1-D slab */
+
+/* The 1-D slab problem of the paper's 1-D case study (Sec. 4.1): the same
+ * vertex diamond-difference operators restricted to x, 2^l points across a
+ * slab of the given width, vacuum on both faces.  Directions: a half-range
+ * set amu[d] > 0 used for both signs of mu with weights w[d]
+ * (2 * sum(w) = 1).  Tables as in tt_problem; mat[c] gives the material of
+ * cell c (2^l - 1 cells).  Host arrays, copied by the library. */
+typedef struct {
+  int l;                    /* 2^l points, 1 <= l <= 24 */
+  double width;             /* slab width; Delta = width / (2^l - 1) */
+  int G, n_mat;
+  const double *sig_t;      /* [n_mat][G] */
+  const double *sig_s;      /* [n_mat][G_to][G_from] */
+  const double *nu_sig_f;   /* [n_mat][G] */
+  const double *chi;        /* [n_mat][G] */
+  const uint8_t *mat;       /* [2^l - 1] */
+  int n_dir;                /* directions per half range */
+  const double *amu;        /* [n_dir] mu > 0 */
+  const double *w;          /* [n_dir] weights of one half range */
+} tt_slab;
+
+/* The k fixed point of Eq. (TT_k_eff_fixed_points) on the slab operators,
+ * TT cores [G][2 (mu < 0, mu > 0)][n_dir][x bits] (the paper's ISTT), with
+ * the options and result of keig_fixed_point (opts->prec as there).
+ * phi_out: NULL or host [G][2^l], the scalar flux sum over both half ranges
+ * of w[d] psi, normalised so that sum(F Psi) = 1.  TT_ENOCONV at max_iter. */
+int keig_slab_fixed_point(tt_ctx *ctx, const tt_slab *slab, const keig_opts *opts, keig_result *out,
+                          double *phi_out);
+
 /* Gradient of a flux functional by generalised perturbation theory (GPT).
  * The functional is J = sum_g sum_v resp_g[g] resp_v[v] phi[g, v] of the
  * scalar flux phi = sum_l w_l Psi[g, l, v] of the eigenvector normalised so
@@ -353,7 +383,9 @@ int keig_gpt(tt_ctx *ctx, const tt_problem *prob, const keig_opts *opts, const d
              double *dJ_dnu_sig_f, double *dJ_dchi, keig_gpt_info *info);
 
 /* Scalar flux of a flux TT (contract the octant and direction cores with the
- * quadrature weights, Appendix B.4) as a TT with cores [G][2 x 3l]. */
+ * quadrature weights, Appendix B.4) as a TT with cores [G][2 x 3l]; for a
+ * slab flux (cores [G][2][n_dir][x bits]) the hemisphere core takes the place
+ * of the octant core and the result has cores [G][2 x l]. */
 int tt_scalar_flux(tt_ctx *ctx, const tt_vec *psi, const double *w_host, int n_dir, tt_vec **phi);
 
 /* ---------------------------------------------------------------- allocation-free inner product */

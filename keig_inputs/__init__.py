@@ -339,3 +339,74 @@ def fissile_response(prob: Problem, group: int = 0):
     resp_g = np.zeros(prob.G)
     resp_g[group] = 1.0
     return resp_g, resp_v
+
+
+# ---------------------------------------------------------------- 1-D slab
+@dataclasses.dataclass
+class Slab:
+    """A 1-D slab k-eigenvalue problem (vacuum on both faces) in the layout
+    the C-ABI ``tt_slab`` takes: 2^l points across ``width``, materials per
+    cell (``mat[c]``, 2^l - 1 cells), tables as in ``Problem``, and a
+    half-range quadrature: ``amu[d] > 0`` with weights ``w[d]`` used for both
+    signs of mu (2 * sum(w) = 1)."""
+
+    name: str
+    l: int
+    width: float
+    G: int
+    sig_t: np.ndarray
+    sig_s: np.ndarray
+    nu_sig_f: np.ndarray
+    chi: np.ndarray
+    mat: np.ndarray
+    amu: np.ndarray
+    w: np.ndarray
+
+    @property
+    def n(self) -> int:
+        return 1 << self.l
+
+    @property
+    def n_mat(self) -> int:
+        return int(self.sig_t.shape[0])
+
+    @property
+    def n_dir(self) -> int:
+        return int(self.amu.size)
+
+    @property
+    def delta(self) -> float:
+        return float(self.width) / (self.n - 1)
+
+    @property
+    def psi_shape(self) -> tuple:
+        """(G, 2, n_dir, n): hemisphere 0 is mu < 0, 1 is mu > 0."""
+        return (self.G, 2, self.n_dir, self.n)
+
+    @property
+    def tt_modes(self) -> List[int]:
+        return [self.G, 2, self.n_dir] + [2] * self.l
+
+
+def gauss_legendre_half(L: int):
+    """Half-range Gauss-Legendre set of an S_L quadrature: the L/2 positive
+    nodes of the L-point Gauss-Legendre rule and their weights halved (so
+    that the weights of all L directions sum to 1)."""
+    if L < 2 or L % 2:
+        raise ValueError("L must be even and >= 2")
+    x, wt = np.polynomial.legendre.leggauss(L)
+    pos = x > 0
+    order = np.argsort(x[pos])
+    return x[pos][order].copy(), 0.5 * wt[pos][order].copy()
+
+
+def pu239_slab(l: int = 10, L: int = 8) -> Slab:
+    """The one-group bare Pu-239 slab of the paper's 1-D case study (Sec. 4.1,
+    cross sections as printed in its table): nu = 3.24, sigma_f = 0.081600,
+    sigma_s = 0.225216, sigma_t = 0.32640 (1/cm), width 3.707444 cm, vacuum
+    faces; exactly critical (k = 1) for the exact transport solution."""
+    amu, w = gauss_legendre_half(L)
+    nu, sf, ss, st = 3.24, 0.081600, 0.225216, 0.32640
+    return Slab(name=f"pu239_slab_l{l}_S{L}", l=l, width=3.707444, G=1,
+                sig_t=np.array([[st]]), sig_s=np.array([[[ss]]]), nu_sig_f=np.array([[nu * sf]]),
+                chi=np.array([[1.0]]), mat=np.zeros(2 ** l - 1, np.uint8), amu=amu, w=w)

@@ -12,5 +12,5 @@ from ._lib import (  # noqa: F401
     KeigError, Context, TTVec, TTOp, lib_path, load,
     tt_ctx_create, tt_vec_create, tt_op_create, tt_round, tt_matvec, tt_solve_local,
     tt_build_operator, keig_fixed_point, keig_default_opts, tt_scalar_flux, tt_dot_noalloc,
-    keig_sensitivities, keig_k_function, keig_batch, keig_alpha, keig_gpt,
+    keig_sensitivities, keig_k_function, keig_batch, keig_alpha, keig_gpt, keig_slab_fixed_point,
 )

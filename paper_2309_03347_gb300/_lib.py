@@ -447,6 +447,55 @@ def keig_fixed_point(ctx: Context, prob, opts: Optional[KeigOpts] = None, want_p
                 psi=TTVec(ctx, h) if want_psi and h.value else None, phi=phi, code=rc)
 
 
+class TTSlab(C.Structure):
+    _fields_ = [
+        ("l", C.c_int), ("width", C.c_double), ("G", C.c_int), ("n_mat", C.c_int),
+        ("sig_t", D), ("sig_s", D), ("nu_sig_f", D), ("chi", D), ("mat", C.POINTER(C.c_uint8)),
+        ("n_dir", C.c_int), ("amu", D), ("w", D),
+    ]
+
+
+class _SlabArrays:
+    """Keeps the contiguous arrays a TTSlab points into alive."""
+
+    def __init__(self, slab):
+        self.arrays = a = dict(
+            sig_t=np.ascontiguousarray(slab.sig_t, np.float64), sig_s=np.ascontiguousarray(slab.sig_s, np.float64),
+            nsf=np.ascontiguousarray(slab.nu_sig_f, np.float64), chi=np.ascontiguousarray(slab.chi, np.float64),
+            mat=np.ascontiguousarray(slab.mat, np.uint8), amu=np.ascontiguousarray(slab.amu, np.float64),
+            w=np.ascontiguousarray(slab.w, np.float64))
+        s = TTSlab()
+        s.l, s.width, s.G, s.n_mat = int(slab.l), float(slab.width), int(slab.G), int(slab.n_mat)
+        s.sig_t, s.sig_s, s.nu_sig_f, s.chi = _dp(a["sig_t"]), _dp(a["sig_s"]), _dp(a["nsf"]), _dp(a["chi"])
+        s.mat = a["mat"].ctypes.data_as(C.POINTER(C.c_uint8))
+        s.n_dir = int(a["amu"].size)
+        s.amu, s.w = _dp(a["amu"]), _dp(a["w"])
+        self.s = s
+
+
+def keig_slab_fixed_point(ctx: Context, slab, opts: Optional[KeigOpts] = None, want_phi: bool = False,
+                          allow_noconv: bool = False):
+    """The k fixed point on a 1-D slab (keig.h: keig_slab_fixed_point);
+    returns dict(k, iters, dk, wall_ms, max_rank, k_hist, phi, code)."""
+    lib = load()
+    if not getattr(lib.keig_slab_fixed_point, "_marshalled", False):
+        lib.keig_slab_fixed_point.argtypes = [C.c_void_p, C.POINTER(TTSlab), C.POINTER(KeigOpts),
+                                              C.POINTER(KeigResult), D]
+        lib.keig_slab_fixed_point.restype = C.c_int
+        lib.keig_slab_fixed_point._marshalled = True
+    sa = _SlabArrays(slab)
+    o = opts if opts is not None else keig_default_opts()
+    res = KeigResult()
+    phi = np.empty((slab.G, slab.n)) if want_phi else None
+    rc = lib.keig_slab_fixed_point(ctx.h, C.byref(sa.s), C.byref(o), C.byref(res),
+                                   _dp(phi) if phi is not None else None)
+    if not (allow_noconv and rc == TT_ENOCONV):
+        ctx.check(rc)
+    it = min(res.iters, 512)
+    return dict(k=res.k, iters=res.iters, dk=res.dk_last, wall_ms=res.wall_ms, max_rank=res.max_rank,
+                k_hist=np.array(res.k_hist[:it]), phi=phi, code=rc)
+
+
 def tt_scalar_flux(ctx: Context, psi: TTVec, w8) -> TTVec:
     w = np.ascontiguousarray(w8, np.float64)
     h = C.c_void_p()

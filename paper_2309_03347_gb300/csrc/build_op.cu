@@ -98,10 +98,77 @@ __global__ void diag_times_op_kernel(const double *__restrict__ mk, int rc0, int
 }
 
 struct Term {
-  std::vector<std::vector<double>> head;  // G x G, 8 x 8, nd x nd factors
-  int fz, fy, fx;                         // indices into the QTT factor list
+  std::vector<std::vector<double>> head;  // G x G, (8 or 2) x (8 or 2), nd x nd factors
+  std::vector<int> f;                     // per spatial axis (outermost first): index into the QTT factor list
   int mask;                               // -1 or index into the mask list
 };
+
+// Sum of rank-1 terms as one TT matrix: head cores h0.. of each term, then
+// the QTT cores of its spatial factors axis by axis (l bits each), each term
+// optionally multiplied row-wise by a diagonal mask TT; partial sums rounded
+// every few terms and at the end at eps_op.
+TT assemble_terms(Ctx *c, const std::vector<Term> &terms, int h0, const std::vector<int> &hsz, int naxes, int l,
+                  const std::vector<std::vector<DBuf>> &qf, const std::vector<std::vector<int>> &qr,
+                  const std::vector<TT> &masks, double eps_op) {
+  const int nh = (int)hsz.size() - h0;  // head cores kept
+  const int d = nh + naxes * l;
+  const int sp0 = nh;  // index of the first spatial core
+  std::vector<int> mo(d), mi(d);
+  for (int k = 0; k < sp0; ++k) mo[k] = mi[k] = hsz[k + h0];
+  for (int k = sp0; k < d; ++k) mo[k] = mi[k] = 2;
+  TT acc;
+  bool have = false;
+  int pending = 0;
+  for (const Term &t : terms) {
+    TT x;
+    x.d = d;
+    x.mo = mo;
+    x.mi = mi;
+    x.n.resize(d);
+    for (int k = 0; k < d; ++k) x.n[k] = mo[k] * mi[k];
+    x.r.assign(d + 1, 1);
+    x.core.resize(d);
+    for (int k = 0; k < sp0; ++k) x.core[k] = upload(c, t.head[k + h0]);
+    for (int a = 0; a < naxes; ++a)
+      for (int b = 0; b < l; ++b) {
+        const int k = sp0 + a * l + b;
+        x.r[k] = qr[t.f[a]][b];
+        x.r[k + 1] = qr[t.f[a]][b + 1];
+        x.core[k].alloc(c, x.csize(k));
+        copy(c, x.core[k].p(), qf[t.f[a]][b].p(), x.csize(k));
+      }
+    if (t.mask >= 0) {
+      // M (Ip (x) ... (x) Ip): core-wise product with the diagonal mask TT
+      const TT &mk = masks[t.mask];
+      for (int q = 0; q < naxes * l; ++q) {
+        const int k = sp0 + q;
+        const int rc0 = mk.r[q], rc1 = mk.r[q + 1], Rs0 = x.r[k], Rs1 = x.r[k + 1];
+        DBuf out(c, (size_t)rc0 * Rs0 * 4 * rc1 * Rs1);
+        const long long tot = (long long)rc0 * Rs0 * 4 * rc1 * Rs1;
+        diag_times_op_kernel<<<(unsigned)std::min<long long>((tot + 255) / 256, 4096), 256, 0, c->stream>>>(
+            mk.core[q].p(), rc0, rc1, x.core[k].p(), Rs0, Rs1, out.p());
+        c->count();
+        TT_CHECK_CUDA(cudaGetLastError());
+        x.core[k] = std::move(out);
+      }
+      for (int q = 1; q < naxes * l; ++q) x.r[sp0 + q] *= mk.r[q];
+      round(c, x, 1e-14, 0);
+    }
+    if (!have) {
+      acc = std::move(x);
+      have = true;
+    } else {
+      acc = add(c, 1.0, acc, 1.0, x);
+      if (++pending >= 4) {
+        round(c, acc, eps_op, 0);
+        pending = 0;
+      }
+    }
+  }
+  TT_REQUIRE(have, "build_operator: operator has no terms");
+  round(c, acc, eps_op, 0);
+  return acc;
+}
 
 }  // namespace
 
@@ -152,7 +219,6 @@ TT assemble_operator(Ctx *c, const tt_problem *p, const OpFactors &F, int kind, 
   // derivative kinds omit the group core (the operator is linear in the group matrix)
   const bool group_core = !(kind == KIND_COLLISION || kind == KIND_SOURCE);
   const int h0 = group_core ? 0 : 1;  // first head factor used
-  const int d = 3 + 3 * l - h0;
   std::vector<Term> terms;
   auto eye = [](int k) {
     std::vector<double> a((size_t)k * k, 0.0);
@@ -173,9 +239,9 @@ TT assemble_operator(Ctx *c, const tt_problem *p, const OpFactors &F, int kind, 
     E[o * 8 + o] = 1.0;
     for (int j = 0; j < 8; ++j) Intg[o * 8 + j] = 1.0;
     if (kind == TT_OP_H) {
-      terms.push_back({{eye(G), E, diag(p->amu, nd)}, F.iIp[pz], F.iIp[py], F.iD[0][px], -1});
-      terms.push_back({{eye(G), E, diag(p->aeta, nd)}, F.iIp[pz], F.iD[1][py], F.iIp[px], -1});
-      terms.push_back({{eye(G), E, diag(p->axi, nd)}, F.iD[2][pz], F.iIp[py], F.iIp[px], -1});
+      terms.push_back({{eye(G), E, diag(p->amu, nd)}, {F.iIp[pz], F.iIp[py], F.iD[0][px]}, -1});
+      terms.push_back({{eye(G), E, diag(p->aeta, nd)}, {F.iIp[pz], F.iD[1][py], F.iIp[px]}, -1});
+      terms.push_back({{eye(G), E, diag(p->axi, nd)}, {F.iD[2][pz], F.iIp[py], F.iIp[px]}, -1});
     }
     for (int m = 0; m < nm; ++m) {
       if (only_mat >= 0 && m != only_mat) continue;
@@ -183,9 +249,9 @@ TT assemble_operator(Ctx *c, const tt_problem *p, const OpFactors &F, int kind, 
       if (nm > 1 && mi < 0) continue;
       if (kind == TT_OP_H || kind == KIND_COLLISION) {
         terms.push_back({{kind == TT_OP_H ? diag(p->sig_t + (size_t)m * G, G) : std::vector<double>(), E, eye(nd)},
-                         F.iIp[pz], F.iIp[py], F.iIp[px], mi});
+                         {F.iIp[pz], F.iIp[py], F.iIp[px]}, mi});
       } else if (kind == KIND_SOURCE) {
-        terms.push_back({{std::vector<double>(), Intg, dirm}, F.iIpN[pz], F.iIpN[py], F.iIpN[px], mi});
+        terms.push_back({{std::vector<double>(), Intg, dirm}, {F.iIpN[pz], F.iIpN[py], F.iIpN[px]}, mi});
       } else {
         std::vector<double> gm((size_t)G * G);
         bool nonzero = false;
@@ -197,69 +263,95 @@ TT assemble_operator(Ctx *c, const tt_problem *p, const OpFactors &F, int kind, 
             nonzero |= v != 0.0;
           }
         if (!nonzero) continue;
-        terms.push_back({{gm, Intg, dirm}, F.iIpN[pz], F.iIpN[py], F.iIpN[px], mi});
+        terms.push_back({{gm, Intg, dirm}, {F.iIpN[pz], F.iIpN[py], F.iIpN[px]}, mi});
       }
     }
   }
-  // ---- assemble each term as a TT matrix and accumulate with rounding
-  const int sp0 = 3 - h0;  // index of the first spatial core
-  std::vector<int> mo(d), mi(d);
-  const int hsz[3] = {G, 8, nd};
-  for (int k = 0; k < sp0; ++k) mo[k] = mi[k] = hsz[k + h0];
-  for (int k = sp0; k < d; ++k) mo[k] = mi[k] = 2;
-  TT acc;
-  bool have = false;
-  int pending = 0;
-  for (const Term &t : terms) {
-    TT x;
-    x.d = d;
-    x.mo = mo;
-    x.mi = mi;
-    x.n.resize(d);
-    for (int k = 0; k < d; ++k) x.n[k] = mo[k] * mi[k];
-    x.r.assign(d + 1, 1);
-    x.core.resize(d);
-    for (int k = 0; k < sp0; ++k) x.core[k] = upload(c, t.head[k + h0]);
-    const int fidx[3] = {t.fz, t.fy, t.fx};
-    for (int a = 0; a < 3; ++a)
-      for (int b = 0; b < l; ++b) {
-        const int k = sp0 + a * l + b;
-        x.r[k] = F.qr[fidx[a]][b];
-        x.r[k + 1] = F.qr[fidx[a]][b + 1];
-        x.core[k].alloc(c, x.csize(k));
-        copy(c, x.core[k].p(), F.qf[fidx[a]][b].p(), x.csize(k));
+  return assemble_terms(c, terms, h0, {G, 8, nd}, 3, l, F.qf, F.qr, F.masks, eps_op);
+}
+
+// 1-D slab operators over the modes [G][2][n_dir][x bits]: the terms of the
+// 3-D operators restricted to x, with a hemisphere core (0: mu < 0, 1: mu > 0)
+// in place of the octant core:
+//   H: I_G (x) E_h (x) diag|mu| (x) Dt_x  +  sum_m diag(sig_t(m)) (x) E_h (x) I (x) M_m^h Ip_x
+//   S: sum_m Sig_s(m)          (x) e_h 1^T (x) 1 w^T (x) M_m^h Ip_x,noBC
+//   F: sum_m chi(m) nsf(m)^T   (x) e_h 1^T (x) 1 w^T (x) M_m^h Ip_x,noBC
+TT assemble_slab_operator(Ctx *c, const tt_slab *s, int kind, double eps_op) {
+  const int l = s->l, n = 1 << l, G = s->G, nd = s->n_dir, nm = s->n_mat;
+  const double del = s->width / (n - 1);
+  std::vector<std::vector<DBuf>> qf;
+  std::vector<std::vector<int>> qr;
+  auto add_factor = [&](std::vector<double> f) {
+    std::vector<int> rk;
+    qf.push_back(qtt_factor(c, f, l, rk));
+    qr.push_back(rk);
+    return (int)qf.size() - 1;
+  };
+  int iD[2], iIp[2], iIpN[2];
+  for (int pos = 0; pos < 2; ++pos) {
+    iD[pos] = add_factor(factor_D(n, del, pos));
+    iIp[pos] = add_factor(factor_Ip(n, pos, false));
+    iIpN[pos] = add_factor(factor_Ip(n, pos, true));
+  }
+  // row masks per (hemisphere, material) when heterogeneous
+  std::vector<TT> masks;
+  std::vector<int> mask_index((size_t)2 * nm, -1);
+  if (nm > 1) {
+    std::vector<double> mv(n);
+    for (int h = 0; h < 2; ++h)
+      for (int m = 0; m < nm; ++m) {
+        int cnt = 0;
+        for (int i = 0; i < n; ++i) {
+          const int mat = s->mat[row_cell(i, h == 1, n)];
+          mv[i] = mat == m ? 1.0 : 0.0;
+          cnt += mat == m;
+        }
+        if (!cnt) continue;
+        DBuf dmv = upload(c, mv);
+        masks.push_back(tt_svd_dense(c, dmv.p(), std::vector<int>(l, 2), 1e-14, 0));
+        mask_index[(size_t)h * nm + m] = (int)masks.size() - 1;
       }
-    if (t.mask >= 0) {
-      // M (Ip (x) Ip (x) Ip): core-wise product with the diagonal mask TT
-      const TT &mk = F.masks[t.mask];
-      for (int q = 0; q < 3 * l; ++q) {
-        const int k = sp0 + q;
-        const int rc0 = mk.r[q], rc1 = mk.r[q + 1], Rs0 = x.r[k], Rs1 = x.r[k + 1];
-        DBuf out(c, (size_t)rc0 * Rs0 * 4 * rc1 * Rs1);
-        const long long tot = (long long)rc0 * Rs0 * 4 * rc1 * Rs1;
-        diag_times_op_kernel<<<(unsigned)std::min<long long>((tot + 255) / 256, 4096), 256, 0, c->stream>>>(
-            mk.core[q].p(), rc0, rc1, x.core[k].p(), Rs0, Rs1, out.p());
-        c->count();
-        TT_CHECK_CUDA(cudaGetLastError());
-        x.core[k] = std::move(out);
-      }
-      for (int q = 1; q < 3 * l; ++q) x.r[sp0 + q] *= mk.r[q];
-      round(c, x, 1e-14, 0);
-    }
-    if (!have) {
-      acc = std::move(x);
-      have = true;
-    } else {
-      acc = add(c, 1.0, acc, 1.0, x);
-      if (++pending >= 4) {
-        round(c, acc, eps_op, 0);
-        pending = 0;
+  }
+  auto eye = [](int k) {
+    std::vector<double> a((size_t)k * k, 0.0);
+    for (int i = 0; i < k; ++i) a[(size_t)i * k + i] = 1.0;
+    return a;
+  };
+  auto diag = [](const double *v, int k) {
+    std::vector<double> a((size_t)k * k, 0.0);
+    for (int i = 0; i < k; ++i) a[(size_t)i * k + i] = v[i];
+    return a;
+  };
+  std::vector<double> dirm((size_t)nd * nd);
+  for (int a = 0; a < nd; ++a)
+    for (int b = 0; b < nd; ++b) dirm[(size_t)a * nd + b] = s->w[b];
+  std::vector<Term> terms;
+  for (int h = 0; h < 2; ++h) {
+    std::vector<double> E(4, 0.0), Intg(4, 0.0);
+    E[h * 2 + h] = 1.0;
+    Intg[h * 2] = Intg[h * 2 + 1] = 1.0;
+    if (kind == TT_OP_H) terms.push_back({{eye(G), E, diag(s->amu, nd)}, {iD[h]}, -1});
+    for (int m = 0; m < nm; ++m) {
+      const int mi = nm > 1 ? mask_index[(size_t)h * nm + m] : -1;
+      if (nm > 1 && mi < 0) continue;
+      if (kind == TT_OP_H) {
+        terms.push_back({{diag(s->sig_t + (size_t)m * G, G), E, eye(nd)}, {iIp[h]}, mi});
+      } else {
+        std::vector<double> gm((size_t)G * G);
+        bool nonzero = false;
+        for (int a = 0; a < G; ++a)
+          for (int b = 0; b < G; ++b) {
+            const double v = kind == TT_OP_S ? s->sig_s[((size_t)m * G + a) * G + b]
+                                             : s->chi[(size_t)m * G + a] * s->nu_sig_f[(size_t)m * G + b];
+            gm[(size_t)a * G + b] = v;
+            nonzero |= v != 0.0;
+          }
+        if (!nonzero) continue;
+        terms.push_back({{gm, Intg, dirm}, {iIpN[h]}, mi});
       }
     }
   }
-  TT_REQUIRE(have, "build_operator: operator has no terms");
-  round(c, acc, eps_op, 0);
-  return acc;
+  return assemble_terms(c, terms, 0, {G, 2, nd}, 1, l, qf, qr, masks, eps_op);
 }
 
 TT build_operator(Ctx *c, const tt_problem *p, int kind, double eps_op) {

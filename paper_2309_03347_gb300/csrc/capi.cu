@@ -453,7 +453,8 @@ int tt_scalar_flux(tt_ctx *ctx, const tt_vec *psi, const double *w_host, int n_d
   return guarded(ctx, [&] {
     TT_REQUIRE(psi && w_host && phi, "null argument");
     const tt::TT &x = psi->t;
-    TT_REQUIRE(x.d >= 4 && x.n[1] == 8 && x.n[2] == n_dir, "tt_scalar_flux: expected cores [G][8][L/8][...]");
+    TT_REQUIRE(x.d >= 4 && (x.n[1] == 8 || x.n[1] == 2) && x.n[2] == n_dir,
+               "tt_scalar_flux: expected cores [G][8 or 2][n_dir][...]");
     tt::Ctx *c = &ctx->c;
     std::vector<double> ones(8, 1.0);
     tt::DBuf d1(c, 8), dw(c, n_dir);
@@ -461,7 +462,7 @@ int tt_scalar_flux(tt_ctx *ctx, const tt_vec *psi, const double *w_host, int n_d
     TT_CHECK_CUDA(cudaMemcpyAsync(dw.p(), w_host, n_dir * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     const int r1 = x.r[1], r2 = x.r[2], r3 = x.r[3];
     tt::DBuf A(c, (size_t)r1 * r2), B(c, (size_t)r2 * r3), W(c, (size_t)r1 * r3);
-    tt::contract_mode(c, x.core[1].p(), r1, 8, r2, d1.p(), A.p());
+    tt::contract_mode(c, x.core[1].p(), r1, x.n[1], r2, d1.p(), A.p());
     tt::contract_mode(c, x.core[2].p(), r2, n_dir, r3, dw.p(), B.p());
     tt::gemm(c, false, false, r1, r3, r2, 1.0, A.p(), r2, 0, B.p(), r3, 0, 0.0, W.p(), r3, 0);
     tt::TT y;
@@ -777,6 +778,62 @@ int keig_sensitivities(tt_ctx *ctx, const tt_problem *prob, const keig_opts *opt
   });
   if (rc == TT_OK && !conv) {
     ctx->c.err = "keig_sensitivities: a fixed point reached max_iter";
+    return TT_ENOCONV;
+  }
+  return rc;
+}
+
+int keig_slab_fixed_point(tt_ctx *ctx, const tt_slab *slab, const keig_opts *opts, keig_result *out,
+                          double *phi_out) {
+  int conv = 0;
+  int rc = guarded(ctx, [&] {
+    TT_REQUIRE(slab && out, "keig_slab_fixed_point: null argument");
+    check_opts(opts);
+    TT_REQUIRE(slab->l >= 1 && slab->l <= 24, "slab: l out of range");
+    TT_REQUIRE(slab->G >= 1 && slab->G <= 4096 && slab->n_mat >= 1 && slab->n_mat <= 255, "slab: bad G or n_mat");
+    TT_REQUIRE(slab->n_dir >= 1 && slab->n_dir <= 4096, "slab: bad n_dir");
+    TT_REQUIRE(std::isfinite(slab->width) && slab->width > 0, "slab: bad width");
+    TT_REQUIRE(slab->sig_t && slab->sig_s && slab->nu_sig_f && slab->chi && slab->mat && slab->amu && slab->w,
+               "slab: null table");
+    const size_t G = slab->G, nm = slab->n_mat, nd = slab->n_dir, n = (size_t)1 << slab->l;
+    check_finite_host(slab->sig_t, nm * G, "sig_t");
+    check_finite_host(slab->sig_s, nm * G * G, "sig_s");
+    check_finite_host(slab->nu_sig_f, nm * G, "nu_sig_f");
+    check_finite_host(slab->chi, nm * G, "chi");
+    check_finite_host(slab->amu, nd, "amu");
+    check_finite_host(slab->w, nd, "w");
+    for (size_t i = 0; i + 1 < n; ++i) TT_REQUIRE(slab->mat[i] < nm, "slab: material index out of range");
+    for (size_t i = 0; i < nd; ++i) TT_REQUIRE(slab->amu[i] > 0, "slab: amu must be positive");
+    const auto t0 = clk::now();
+    tt::Ctx *c = &ctx->c;
+    memset(out, 0, sizeof(*out));
+    tt::TT H, S, F;
+    {
+      tt::PhaseTimer pt(c, "keig.build_ops");
+      H = tt::assemble_slab_operator(c, slab, TT_OP_H, opts->eps_op);
+      S = tt::assemble_slab_operator(c, slab, TT_OP_S, opts->eps_op);
+      F = tt::assemble_slab_operator(c, slab, TT_OP_F, opts->eps_op);
+    }
+    KeigOps ops = make_ops(c, std::move(H), std::move(S), std::move(F), opts);
+    tt::TT psi;
+    conv = run_fixed_point(c, ops, opts, out, psi, t0, 0);
+    if (phi_out) {
+      tt_vec tmp{c, std::move(psi)};
+      tt_vec *phi = nullptr;
+      const int r2 = tt_scalar_flux(ctx, &tmp, slab->w, slab->n_dir, &phi);
+      if (r2 != TT_OK) throw tt::Error(r2, ctx->c.err);
+      const size_t len = G * n;
+      tt::DBuf dst(c, len);
+      tt::to_dense(c, phi->t, dst.p(), len);
+      TT_CHECK_CUDA(cudaMemcpyAsync(phi_out, dst.p(), len * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      c->sync();
+      tt_vec_destroy(phi);
+    }
+    c->sync();
+    out->wall_ms = std::chrono::duration<double, std::milli>(clk::now() - t0).count();
+  });
+  if (rc == TT_OK && !conv) {
+    ctx->c.err = "keig_slab_fixed_point: max_iter reached";
     return TT_ENOCONV;
   }
   return rc;

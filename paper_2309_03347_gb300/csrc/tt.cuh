@@ -117,5 +117,7 @@ enum { KIND_COLLISION = 10, KIND_SOURCE = 11 };
 OpFactors make_factors(Ctx *c, const tt_problem *p);
 TT assemble_operator(Ctx *c, const tt_problem *p, const OpFactors &F, int kind, int only_mat, double eps_op);
 TT build_operator(Ctx *c, const tt_problem *p, int kind, double eps_op);
+// H, S or F of a 1-D slab over the modes [G][2][n_dir][x bits]
+TT assemble_slab_operator(Ctx *c, const tt_slab *s, int kind, double eps_op);
 
 }  // namespace tt
