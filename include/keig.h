@@ -234,6 +234,8 @@ typedef struct {
   tt_prec prec;
   double eps_op;     /* operator rounding tolerance */
   const double *psi0_cores; /* optional host TT initial guess (rank-1 cores), NULL = ones */
+  int mv_kind;       /* product B = (S + F/k) Psi: 0 the AMEn product (the paper's choice),
+                        1 the exact TT product (core-wise Kronecker) rounded at eps / rmax */
 } keig_opts;
 
 typedef struct {
@@ -248,7 +250,7 @@ typedef struct {
 
 /* Fill opts with defaults (eps 1e-7, rmax 64, tol_k 1e-9, tol_psi 1e-5,
  * max_iter 400, solve_sweeps 2, mv_sweeps 2, kick 4, scheme 0, FP64,
- * eps_op 1e-12). */
+ * eps_op 1e-12, AMEn product). */
 int keig_default_opts(keig_opts *opts);
 
 /* The QTT fixed point of Eq. (TT_k_eff_fixed_points):

@@ -498,6 +498,7 @@ int keig_default_opts(keig_opts *o) {
   o->prec = TT_FP64;
   o->eps_op = 1e-12;
   o->psi0_cores = nullptr;
+  o->mv_kind = 0;
   return TT_OK;
 }
 
@@ -513,6 +514,7 @@ void check_opts(const keig_opts *opts) {
              "keig: prec must be TT_FP64, TT_FP32_REFINED or TT_TF32_SPLIT");
   TT_REQUIRE(opts->eps > 0 && opts->eps < 1 && opts->max_iter >= 1, "keig: bad eps/max_iter");
   TT_REQUIRE(opts->scheme == 0 || opts->scheme == 1, "keig: scheme must be 0 or 1");
+  TT_REQUIRE(opts->mv_kind == 0 || opts->mv_kind == 1, "keig: mv_kind must be 0 or 1");
 }
 
 // The operators of one problem, forward or transposed (adjoint).
@@ -577,7 +579,11 @@ bool run_fixed_point(tt::Ctx *c, KeigOps &ops, const keig_opts *opts, keig_resul
     ops.RHS.invalidate();
     k_in_op = k;
     tt::SolveStats mst, sst;
-    {
+    if (opts->mv_kind == 1) {
+      tt::PhaseTimer pt(c, "keig.mv_exact");
+      B = tt::matvec_exact(c, ops.RHS.t, psi);
+      tt::round(c, B, opts->eps, opts->rmax);
+    } else {
       tt::PhaseTimer pt(c, "keig.mv");
       tt::amen_mv(c, ops.RHS, psi, B, opts->eps, opts->rmax, opts->mv_sweeps, opts->kick, seed + 1000 + it, &mst);
     }

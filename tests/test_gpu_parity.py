@@ -300,6 +300,21 @@ def test_keig_matches_oracle(ctx, case):
     assert rel(res["phi"], ref["phi"]) < 1e-5
 
 
+def test_keig_exact_product_matches_oracle(ctx):
+    # solver variant: the exact TT product rounded at eps in place of the
+    # AMEn product (Sec. 3.5 compares the two); same fixed point
+    import dataclasses
+    p = dataclasses.replace(ki.config(0), side=(2.0,) * 3)
+    ref = _oracle_keig(p)
+    o = K.keig_default_opts()
+    o.eps, o.rmax, o.tol_k, o.tol_psi, o.max_iter = 1e-10, 0, 1e-11, 1e-7, 200
+    o.solve_sweeps, o.mv_sweeps = 4, 4
+    o.mv_kind = 1
+    res = K.keig_fixed_point(ctx, p, o, want_phi=True)
+    assert abs(res["k"] - ref["k"]) / ref["k"] < 1e-6
+    assert rel(res["phi"], ref["phi"]) < 1e-5
+
+
 @pytest.mark.slow
 def test_keig_config0_vacuum(ctx):
     # dominance ratio 0.956: about 200 power iterations to 1e-7 in k
