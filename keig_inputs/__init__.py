@@ -155,6 +155,7 @@ class Problem:
     eps: float = 1e-10
     rmax: int = 64
     inv_v: Optional[np.ndarray] = None
+    sig_s1: Optional[np.ndarray] = None  # [m, g_to, g_from] P1 scattering moments (linear anisotropy)
 
     @property
     def n(self) -> int:
@@ -410,3 +411,11 @@ def pu239_slab(l: int = 10, L: int = 8) -> Slab:
     return Slab(name=f"pu239_slab_l{l}_S{L}", l=l, width=3.707444, G=1,
                 sig_t=np.array([[st]]), sig_s=np.array([[[ss]]]), nu_sig_f=np.array([[nu * sf]]),
                 chi=np.array([[1.0]]), mat=np.zeros(2 ** l - 1, np.uint8), amu=amu, w=w)
+
+
+def with_linear_anisotropy(prob: Problem, mu_bar: float) -> Problem:
+    """The same problem with linearly anisotropic scattering: P1 moments
+    sig_s1 = mu_bar * sig_s (mu_bar: mean scattering cosine, |mu_bar| < 1/3
+    keeps the P1 kernel 1 + 3 mu_bar cos non-negative)."""
+    return dataclasses.replace(prob, sig_s1=mu_bar * np.asarray(prob.sig_s, dtype=np.float64),
+                               name=prob.name + f"_p1_{mu_bar:g}")

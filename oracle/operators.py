@@ -115,6 +115,17 @@ def assemble(prob):
             f_t = _kron(np.outer(prob.chi[m], prob.nu_sig_f[m]), intg, dirm, mask @ spat_nobc)
             S = s_t if S is None else S + s_t
             F = f_t if F is None else F + f_t
+            s1 = getattr(prob, "sig_s1", None)
+            if s1 is not None:
+                # linear anisotropy (N_s = 1 of the moment operators, weights
+                # summing to 1): row (o, d) gains 3 Omega_a(o, d) sum_{o', d'}
+                # w_d' Omega_a(o', d') for each axis a, with the P1 group matrix
+                for bit, cos in ((1, q.amu), (2, q.aeta), (4, q.axi)):
+                    sgn = np.array([1.0 if (oo & bit) else -1.0 for oo in range(8)])
+                    octm = np.zeros((8, 8))
+                    octm[o, :] = sgn[o] * sgn
+                    dirp = np.outer(cos, cos * q.w8)
+                    S = S + _kron(3.0 * np.asarray(s1[m]), octm, dirp, mask @ spat_nobc)
         for t in terms:
             H = t if H is None else H + t
     return H.tocsr(), S.tocsr(), F.tocsr()

@@ -19,6 +19,12 @@
  *   - the scattering and fission operators S, F (Sec. 3.2.2) applied to the
  *     scalar flux phi = sum_l w_l psi_l, averaged over the 8 corners of the
  *     upstream cell, zero on inflow-face rows (the "noBC" interpolation);
+ *   - optional linearly anisotropic scattering (N_s = 1 of the moment
+ *     operators L^N, L^{N,+} of Appendix A.2, quadrature weights summing to
+ *     1): the source of direction l gains
+ *       3 sum_a Omega_a(l) sum_g' sig_s1[g][g'] Jbar_a(g', c),
+ *     J_a = sum_l w_l Omega_a(l) psi_l (signed cosines), averaged over the
+ *     8 corners of the upstream cell like phi;
  *   - the k fixed point of Eq. (k_eff_fixed_points):
  *       Psi' = H^{-1}(S + F/k) Psi,  k' = k * sum(F Psi') / sum(F Psi).
  *
@@ -48,6 +54,7 @@ typedef struct {
   const double *w8;               /* [L/8] weights (sum over all L = 1) */
   int bc[6];                      /* x-,x+,y-,y+,z-,z+ : must be 0 (vacuum) */
   int threads;                    /* <= 0: library default */
+  const double *sig_s1;           /* [n_mat][G_to][G_from] P1 scattering moments, or NULL */
 } oracle_problem;
 
 static inline int sgn_bit(int o, int axis) { return (o >> axis) & 1; }
@@ -236,6 +243,56 @@ static void cell_sources(const oracle_problem *p, const double *pbar, double *qs
   }
 }
 
+/* signed cosine of direction l = o*(L/8) + d along axis a (0 x, 1 y, 2 z) */
+static inline double cosine(const oracle_problem *p, int ell, int a) {
+  const int m8 = p->L / 8, o = ell / m8, d = ell % m8;
+  const double c = a == 0 ? p->amu[d] : a == 1 ? p->aeta[d] : p->axi[d];
+  return sgn_bit(o, a) ? c : -c;
+}
+
+/* first angular moments J[a][g][v] = sum_l w_l Omega_a(l) psi[g][l][v] */
+static void current(const oracle_problem *p, const double *psi, double *J) {
+  const int n = 1 << p->l;
+  const size_t n3 = (size_t)n * n * n;
+  const int m8 = p->L / 8, G = p->G;
+  memset(J, 0, sizeof(double) * 3 * G * n3);
+  for (int a = 0; a < 3; ++a)
+    for (int g = 0; g < G; ++g)
+      for (int ell = 0; ell < p->L; ++ell) {
+        const double w = p->w8[ell % m8] * cosine(p, ell, a);
+        const double *ps = psi + ((size_t)g * p->L + ell) * n3;
+        double *jj = J + ((size_t)a * G + g) * n3;
+        for (size_t v = 0; v < n3; ++v) jj[v] += w * ps[v];
+      }
+}
+
+/* P1 cell sources q1[a][g][c] = sum_g' sig_s1[m][g][g'] Jbar[a][g'][c] */
+static void p1_sources(const oracle_problem *p, const double *Jbar, double *q1) {
+  const int n = 1 << p->l, nc = n - 1, G = p->G;
+  const size_t c3 = (size_t)nc * nc * nc;
+  for (int a = 0; a < 3; ++a)
+    for (size_t c = 0; c < c3; ++c) {
+      const int m = p->mat[c];
+      for (int g = 0; g < G; ++g) {
+        double s = 0.0;
+        for (int gp = 0; gp < G; ++gp)
+          s += p->sig_s1[((size_t)m * G + g) * G + gp] * Jbar[((size_t)a * G + gp) * c3 + c];
+        q1[((size_t)a * G + g) * c3 + c] = s;
+      }
+    }
+}
+
+/* per-cell scattering source of direction l: q0[c] + 3 sum_a Omega_a(l) q1[a][g][c] */
+static void direction_source(const oracle_problem *p, int g, int ell, const double *q0, const double *q1,
+                             double *out) {
+  const int n = 1 << p->l, nc = n - 1, G = p->G;
+  const size_t c3 = (size_t)nc * nc * nc;
+  const double ox = 3.0 * cosine(p, ell, 0), oy = 3.0 * cosine(p, ell, 1), oz = 3.0 * cosine(p, ell, 2);
+  const double *qx = q1 + ((size_t)0 * G + g) * c3, *qy = q1 + ((size_t)1 * G + g) * c3,
+               *qz = q1 + ((size_t)2 * G + g) * c3;
+  for (size_t c = 0; c < c3; ++c) out[c] = q0[c] + ox * qx[c] + oy * qy[c] + oz * qz[c];
+}
+
 /* Spread a per-cell source onto the rows of direction l (octant o): row v
  * takes the value of its upstream cell, inflow-face rows are zero. */
 static void rows_from_cells(const oracle_problem *p, int o, const double *qc, double *rows) {
@@ -265,12 +322,33 @@ void oracle_apply_SF(const oracle_problem *p, const double *psi, double *out_s, 
   scalar_flux(p, psi, phi);
   cell_average(p, phi, pbar);
   cell_sources(p, pbar, qs, qf);
+  double *J = NULL, *Jbar = NULL, *q1 = NULL, *qd = NULL;
+  if (p->sig_s1) {
+    J = (double *)malloc(sizeof(double) * 3 * p->G * n3);
+    Jbar = (double *)malloc(sizeof(double) * 3 * p->G * c3);
+    q1 = (double *)malloc(sizeof(double) * 3 * p->G * c3);
+    qd = (double *)malloc(sizeof(double) * c3);
+    current(p, psi, J);
+    for (int a = 0; a < 3; ++a) cell_average(p, J + (size_t)a * p->G * n3, Jbar + (size_t)a * p->G * c3);
+    p1_sources(p, Jbar, q1);
+  }
   for (int g = 0; g < p->G; ++g)
     for (int ell = 0; ell < p->L; ++ell) {
       const size_t off = ((size_t)g * p->L + ell) * n3;
-      if (out_s) rows_from_cells(p, ell / m8, qs + (size_t)g * c3, out_s + off);
+      if (out_s) {
+        if (p->sig_s1) {
+          direction_source(p, g, ell, qs + (size_t)g * c3, q1, qd);
+          rows_from_cells(p, ell / m8, qd, out_s + off);
+        } else {
+          rows_from_cells(p, ell / m8, qs + (size_t)g * c3, out_s + off);
+        }
+      }
       if (out_f) rows_from_cells(p, ell / m8, qf + (size_t)g * c3, out_f + off);
     }
+  free(J);
+  free(Jbar);
+  free(q1);
+  free(qd);
   free(phi);
   free(pbar);
   free(qs);
@@ -340,6 +418,13 @@ int oracle_keig(const oracle_problem *p, const oracle_keig_opts *opt, const doub
   double *acc = (double *)malloc(sizeof(double) * nthr * n3);
   double *work = (double *)malloc(sizeof(double) * nthr * 3 * n3);
   uint8_t *fmask = (uint8_t *)malloc(8 * n3);
+  /* linearly anisotropic scattering: first moments and their sources */
+  const int p1 = p->sig_s1 != NULL;
+  double *J = p1 ? (double *)calloc((size_t)3 * G * n3, sizeof(double)) : NULL;
+  double *Jbar = p1 ? (double *)calloc((size_t)3 * G * c3, sizeof(double)) : NULL;
+  double *q1 = p1 ? (double *)malloc(sizeof(double) * 3 * G * c3) : NULL;
+  double *accJ = p1 ? (double *)malloc(sizeof(double) * nthr * 3 * n3) : NULL;
+  double *qd = p1 ? (double *)malloc(sizeof(double) * nthr * c3) : NULL;
 
   /* inflow Dirichlet masks per octant (all inflow-face vertices) */
   for (int o = 0; o < 8; ++o) {
@@ -354,6 +439,7 @@ int oracle_keig(const oracle_problem *p, const oracle_keig_opts *opt, const doub
   if (psi0) {
     if (keep_psi) memcpy(psi, psi0, sizeof(double) * G * L * n3);
     scalar_flux(p, psi0, phi);
+    if (p1) current(p, psi0, J);
   } else {
     memcpy(phi, phi0, sizeof(double) * G * n3);
   }
@@ -363,6 +449,10 @@ int oracle_keig(const oracle_problem *p, const oracle_keig_opts *opt, const doub
   /* normalise so that sum(F Psi) = 1 */
   for (size_t v = 0; v < (size_t)G * n3; ++v) phi[v] /= P;
   for (size_t v = 0; v < (size_t)G * c3; ++v) pbar[v] /= P;
+  if (p1) {
+    for (size_t v = 0; v < (size_t)3 * G * n3; ++v) J[v] /= P;
+    for (int a = 0; a < 3; ++a) cell_average(p, J + (size_t)a * G * n3, Jbar + (size_t)a * G * c3);
+  }
   if (keep_psi)
     for (size_t v = 0; v < (size_t)G * L * n3; ++v) psi[v] /= P;
 
@@ -371,9 +461,12 @@ int oracle_keig(const oracle_problem *p, const oracle_keig_opts *opt, const doub
   for (it = 0; it < opt->max_iter; ++it) {
     cell_sources(p, pbar, qs, qf);
     for (size_t v = 0; v < (size_t)G * c3; ++v) qs[v] += qf[v] / k;
+    if (p1) p1_sources(p, Jbar, q1);
     double *phin = (double *)calloc((size_t)G * n3, sizeof(double));
+    double *Jn = p1 ? (double *)calloc((size_t)3 * G * n3, sizeof(double)) : NULL;
     for (int g = 0; g < G; ++g) {
       memset(acc, 0, sizeof(double) * nthr * n3);
+      if (p1) memset(accJ, 0, sizeof(double) * nthr * 3 * n3);
 #pragma omp parallel num_threads(nthr)
       {
         const int t = omp_get_thread_num();
@@ -383,7 +476,13 @@ int oracle_keig(const oracle_problem *p, const oracle_keig_opts *opt, const doub
 #pragma omp for schedule(static)
         for (int ell = 0; ell < L; ++ell) {
           const int o = ell / m8, d = ell % m8;
-          rows_from_cells(p, o, qs + (size_t)g * c3, rows);
+          if (p1) {
+            double *qt = qd + (size_t)t * c3;
+            direction_source(p, g, ell, qs + (size_t)g * c3, q1, qt);
+            rows_from_cells(p, o, qt, rows);
+          } else {
+            rows_from_cells(p, o, qs + (size_t)g * c3, rows);
+          }
           /* vacuum inflow faces: psi = 0 there (the face rows of H form a
            * homogeneous triangular system with positive diagonal) */
           for (size_t v = 0; v < n3; ++v) fixv[v] = 0.0;
@@ -391,14 +490,29 @@ int oracle_keig(const oracle_problem *p, const oracle_keig_opts *opt, const doub
           double *a = acc + (size_t)t * n3;
           const double w = p->w8[d];
           for (size_t v = 0; v < n3; ++v) a[v] += w * out[v];
+          if (p1)
+            for (int ax = 0; ax < 3; ++ax) {
+              double *aj = accJ + ((size_t)t * 3 + ax) * n3;
+              const double wc = w * cosine(p, ell, ax);
+              for (size_t v = 0; v < n3; ++v) aj[v] += wc * out[v];
+            }
           if (keep_psi) memcpy(psi_new + ((size_t)g * L + ell) * n3, out, sizeof(double) * n3);
         }
       }
       for (int t = 0; t < nthr; ++t)
         for (size_t v = 0; v < n3; ++v) phin[(size_t)g * n3 + v] += acc[(size_t)t * n3 + v];
+      if (p1)
+        for (int ax = 0; ax < 3; ++ax)
+          for (int t = 0; t < nthr; ++t)
+            for (size_t v = 0; v < n3; ++v)
+              Jn[((size_t)ax * G + g) * n3 + v] += accJ[((size_t)t * 3 + ax) * n3 + v];
     }
     memcpy(phi, phin, sizeof(double) * G * n3);
     free(phin);
+    if (p1) {
+      memcpy(J, Jn, sizeof(double) * 3 * G * n3);
+      free(Jn);
+    }
     cell_average(p, phi, pbar);
     const double Pn = production(p, pbar); /* previous iterate had P = 1 */
     const double kn = k * Pn;
@@ -406,6 +520,10 @@ int oracle_keig(const oracle_problem *p, const oracle_keig_opts *opt, const doub
     k = kn;
     for (size_t v = 0; v < (size_t)G * n3; ++v) phi[v] /= Pn;
     for (size_t v = 0; v < (size_t)G * c3; ++v) pbar[v] /= Pn;
+    if (p1) {
+      for (size_t v = 0; v < (size_t)3 * G * n3; ++v) J[v] /= Pn;
+      for (int a = 0; a < 3; ++a) cell_average(p, J + (size_t)a * G * n3, Jbar + (size_t)a * G * c3);
+    }
     if (keep_psi) {
       for (size_t v = 0; v < (size_t)G * L * n3; ++v) psi_new[v] /= Pn;
       double *t = psi;
@@ -432,6 +550,11 @@ int oracle_keig(const oracle_problem *p, const oracle_keig_opts *opt, const doub
   free(acc);
   free(work);
   free(fmask);
+  free(J);
+  free(Jbar);
+  free(q1);
+  free(accJ);
+  free(qd);
   return dk < opt->tol_k ? 0 : 1;
 }
 

@@ -43,7 +43,7 @@ class _Problem(C.Structure):
         ("mat", C.POINTER(C.c_uint8)), ("L", C.c_int),
         ("amu", C.POINTER(C.c_double)), ("aeta", C.POINTER(C.c_double)),
         ("axi", C.POINTER(C.c_double)), ("w8", C.POINTER(C.c_double)),
-        ("bc", C.c_int * 6), ("threads", C.c_int),
+        ("bc", C.c_int * 6), ("threads", C.c_int), ("sig_s1", C.POINTER(C.c_double)),
     ]
 
 
@@ -106,6 +106,11 @@ class OracleProblem:
         for i in range(6):
             s.bc[i] = int(prob.bc[i])
         s.threads = int(threads)
+        if getattr(prob, "sig_s1", None) is not None:
+            self._keep["sig_s1"] = np.ascontiguousarray(prob.sig_s1, dtype=np.float64)
+            s.sig_s1 = _dp(self._keep["sig_s1"])
+        else:
+            s.sig_s1 = None
         self.s = s
         self.shape = prob.psi_shape
 

@@ -264,3 +264,38 @@ def test_functional_gradients_gpt_match_finite_differences():
     # the normalisation term matters: without -J sum(dF Psi) the fission
     # derivatives would be wrong
     assert np.abs(gp["nu_sig_f"]).max() > 1e-3 * scale
+
+
+def test_linear_anisotropy_oracle():
+    # linearly anisotropic scattering (N_s = 1): the stencil's per-direction
+    # sources equal the Kronecker assembly, the power iteration equals the
+    # library eigensolve, an isotropic flux feels no P1 source, mu_bar = 0
+    # reproduces isotropic scattering exactly, and forward scattering (which
+    # lowers the transport cross section) raises the leakage of a small bare
+    # system, so k falls as mu_bar grows
+    import dataclasses
+    import scipy.sparse.linalg as spla
+    p0 = dataclasses.replace(ki.fissile_box(l=2, G=2, order=4, seed=1003, half_width=1), side=(2.0,) * 3)
+    ks = []
+    for mu in (-0.2, 0.0, 0.2):
+        p = ki.with_linear_anisotropy(p0, mu)
+        o = T.OracleProblem(p)
+        H, S, F = O.assemble(p)
+        psi = np.random.default_rng(5).standard_normal(H.shape[0])
+        s_c, _ = o.apply_SF(psi)
+        assert np.abs(S @ psi - s_c.ravel()).max() < 1e-13
+        iso = np.broadcast_to(np.random.default_rng(6).standard_normal((p.G, 1, p.n, p.n, p.n)),
+                              p.psi_shape).ravel()
+        s_iso, _ = o.apply_SF(iso)
+        s_ref, _ = T.OracleProblem(p0).apply_SF(iso)
+        assert np.abs(s_iso - s_ref).max() < 1e-13
+        r = o.keig(tol_k=1e-13, max_iter=100000)
+        lu = spla.splu((H - S).tocsc())
+        N = H.shape[0]
+        vals, _ = spla.eigs(spla.LinearOperator((N, N), matvec=lambda x: lu.solve(F @ x), dtype=np.float64), k=1,
+                            which="LM", tol=1e-14, v0=np.ones(N))
+        assert abs(r["k"] - np.real(vals[0])) < 1e-11 * r["k"]
+        ks.append(r["k"])
+    assert ks[0] > ks[1] > ks[2]
+    k_iso = T.OracleProblem(p0).keig(tol_k=1e-13, max_iter=100000)["k"]
+    assert abs(ks[1] - k_iso) < 1e-14 * k_iso
