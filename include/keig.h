@@ -162,6 +162,12 @@ typedef struct {
   const double *amu, *aeta, *axi; /* [n_dir] absolute direction cosines */
   const double *w;          /* [n_dir] weights of one octant, 8*sum(w) = 1 */
   int bc[6];                /* x-,x+,y-,y+,z-,z+; only 0 (vacuum) is accepted */
+  const double *sig_s1;     /* [n_mat][G_to][G_from] P1 scattering moments (linearly anisotropic
+                               scattering, N_s = 1 of the moment operators L^N, L^{N,+} of
+                               Appendix A.2 with weights summing to 1: direction l's source gains
+                               3 sum_a Omega_a(l) sum_l' w_l' Omega_a(l') (sig_s1 psi_l')), or NULL
+                               (isotropic, the paper's case).  Enters S only; the derivative
+                               outputs of keig_sensitivities / keig_gpt cover sig_s (P0) */
 } tt_problem;
 
 typedef enum {

@@ -262,8 +262,28 @@ TT assemble_operator(Ctx *c, const tt_problem *p, const OpFactors &F, int kind, 
             gm[(size_t)a * G + b] = v;
             nonzero |= v != 0.0;
           }
-        if (!nonzero) continue;
-        terms.push_back({{gm, Intg, dirm}, {F.iIpN[pz], F.iIpN[py], F.iIpN[px]}, mi});
+        if (nonzero) terms.push_back({{gm, Intg, dirm}, {F.iIpN[pz], F.iIpN[py], F.iIpN[px]}, mi});
+        if (kind == TT_OP_S && p->sig_s1) {
+          // linear anisotropy: for each axis a, row (o, d) gains 3 Omega_a(o, d)
+          // sum_{o', d'} w_d' Omega_a(o', d') (P1 group matrix): a rank-1 angular
+          // factor (sign pattern over octants) (x) (|Omega_a| (|Omega_a| w)^T)
+          std::vector<double> g1((size_t)G * G);
+          bool nz1 = false;
+          for (size_t e = 0; e < (size_t)G * G; ++e) {
+            g1[e] = 3.0 * p->sig_s1[(size_t)m * G * G + e];
+            nz1 |= g1[e] != 0.0;
+          }
+          if (!nz1) continue;
+          const double *cosv[3] = {p->amu, p->aeta, p->axi};
+          for (int a = 0; a < 3; ++a) {
+            std::vector<double> octm(64, 0.0), dirp((size_t)nd * nd);
+            const double so = (o >> a) & 1 ? 1.0 : -1.0;
+            for (int j = 0; j < 8; ++j) octm[o * 8 + j] = so * ((j >> a) & 1 ? 1.0 : -1.0);
+            for (int x = 0; x < nd; ++x)
+              for (int y = 0; y < nd; ++y) dirp[(size_t)x * nd + y] = cosv[a][x] * cosv[a][y] * p->w[y];
+            terms.push_back({{g1, octm, dirp}, {F.iIpN[pz], F.iIpN[py], F.iIpN[px]}, mi});
+          }
+        }
       }
     }
   }

@@ -315,6 +315,24 @@ def test_keig_exact_product_matches_oracle(ctx):
     assert rel(res["phi"], ref["phi"]) < 1e-5
 
 
+@pytest.mark.parametrize("mu_bar", [-0.2, 0.25])
+def test_keig_linear_anisotropy_matches_oracle(ctx, mu_bar):
+    # linearly anisotropic scattering (N_s = 1): the S operator gains the
+    # P1 terms; the QTT fixed point must reproduce the oracle's eigenpair
+    import dataclasses
+    p = ki.with_linear_anisotropy(
+        dataclasses.replace(ki.fissile_box(l=3, G=2, order=4, seed=1003, half_width=2), side=(3.0,) * 3), mu_bar)
+    H, S, F = O.assemble(p)
+    A = K.tt_build_operator(ctx, p, 1, 1e-13)
+    x = ki.random_cores(p.tt_modes, [1] + [2] * (len(p.tt_modes) - 1) + [1], 44)
+    y = K.tt_matvec(ctx, A, _vec(ctx, x), 1.0, K.TT_MV_EXACT, -1.0)
+    assert rel(y.dense_cuda().cpu().numpy().ravel(), S @ R.full(x).ravel()) < 1e-11
+    ref = _oracle_keig(p)
+    res = _keig_full_rank(ctx, p, 200, prec=K.TT_FP32_REFINED)
+    assert abs(res["k"] - ref["k"]) / ref["k"] < 1e-6
+    assert rel(res["phi"], ref["phi"]) < 1e-5
+
+
 @pytest.mark.slow
 def test_keig_config0_vacuum(ctx):
     # dominance ratio 0.956: about 200 power iterations to 1e-7 in k
