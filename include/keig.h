@@ -183,9 +183,11 @@ typedef enum {
                          three-term split A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi */
   TT_BF16_SPLIT = 2,  /* reserved: contractions on tensor cores (not built) */
   TT_FP32_REFINED = 3 /* linear solves: Krylov iterations of each local system with FP32 contractions,
-                         wrapped in FP64 iterative refinement (FP64 residual, FP32 correction solve)
-                         until the FP64 residual meets the tolerance; products, QR/SVD, k and all
-                         interfaces stay FP64 */
+                         wrapped in FP64 iterative refinement (FP64 residual, FP32 correction solve,
+                         one persistent GMRES kernel per correction) until the FP64 residual meets
+                         the tolerance; products, QR, k and all interfaces stay FP64.  (In every
+                         precision the SVDs of the truncations find their rotations in FP32 and
+                         refine them by FP64 products; the truncation error stays exact.) */
 } tt_prec;
 
 /* Build H, S or F as a TT matrix with cores over the modes
