@@ -251,14 +251,28 @@ def main():
     ms_step = max_over_ranks(float(np.median(ms)), dist, "cuda")
 
     # ---- end to end: host wall time including the scalar-flux readback
+    # inputs (the problem tables) and the scalar-flux result in pinned host memory
+    pins = []  # keep the pinned tensors alive for the arrays that view them
+
+    def pinned(a):
+        a = np.ascontiguousarray(a)
+        t = torch.empty(a.shape, dtype=getattr(torch, str(a.dtype)), pin_memory=True)
+        pins.append(t)
+        out = t.numpy()
+        out[...] = a
+        return out
+    import dataclasses
+    p_pin = dataclasses.replace(p, sig_t=pinned(p.sig_t), sig_s=pinned(p.sig_s), nu_sig_f=pinned(p.nu_sig_f),
+                                chi=pinned(p.chi), mat=pinned(p.mat))
+    phi_pin = pinned(np.zeros((p.G, p.n, p.n, p.n)))
     e2e = []
     for _ in range(max(1, args.steps)):
         flush.fill_(1.0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        r = step(want_phi=True)
+        r = K.keig_fixed_point(ctx, p_pin, opts, allow_noconv=True, phi_out=phi_pin)
         e2e.append(time.perf_counter() - t0)
-    phi_bytes = r["phi"].nbytes
+    phi_bytes = phi_pin.nbytes
     in_bytes = sum(x.nbytes for x in (p.sig_t, p.sig_s, p.nu_sig_f, p.chi, p.mat)) + 4 * p.quad.amu.nbytes
 
     # ---- one instrumented step: per-launch device time of the contraction GEMM

@@ -431,9 +431,11 @@ def keig_default_opts() -> KeigOpts:
 
 
 def keig_fixed_point(ctx: Context, prob, opts: Optional[KeigOpts] = None, want_psi: bool = False,
-                     want_phi: bool = False, allow_noconv: bool = False, psi0=None):
+                     want_phi: bool = False, allow_noconv: bool = False, psi0=None, phi_out=None):
     """Run the QTT fixed point; returns dict(k, iters, dk, wall_ms, max_rank,
-    k_hist, t_hist, psi (TTVec or None), phi (host array or None), code)."""
+    k_hist, t_hist, psi (TTVec or None), phi (host array or None), code).
+    phi_out: optional preallocated host array (G, n, n, n) float64 for the
+    scalar flux (e.g. in pinned memory); implies want_phi."""
     pa = _ProblemArrays(prob)
     o = opts if opts is not None else keig_default_opts()
     keep = None
@@ -442,7 +444,12 @@ def keig_fixed_point(ctx: Context, prob, opts: Optional[KeigOpts] = None, want_p
         o.psi0_cores = _dp(keep)
     res = KeigResult()
     h = C.c_void_p()
-    phi = np.empty((prob.G, prob.n, prob.n, prob.n)) if want_phi else None
+    if phi_out is not None:
+        if phi_out.dtype != np.float64 or not phi_out.flags.c_contiguous or phi_out.size != prob.G * prob.n ** 3:
+            raise KeigError(TT_EINVAL, "keig_fixed_point: phi_out must be a contiguous float64 (G, n, n, n) array")
+        phi = phi_out
+    else:
+        phi = np.empty((prob.G, prob.n, prob.n, prob.n)) if want_phi else None
     rc = ctx.lib.keig_fixed_point(ctx.h, C.byref(pa.s), C.byref(o), C.byref(res),
                                   C.byref(h) if want_psi else None, _dp(phi) if phi is not None else None)
     if not (allow_noconv and rc == TT_ENOCONV):
