@@ -168,6 +168,10 @@ typedef struct {
                                3 sum_a Omega_a(l) sum_l' w_l' Omega_a(l') (sig_s1 psi_l')), or NULL
                                (isotropic, the paper's case).  Enters S only; the derivative
                                outputs of keig_sensitivities / keig_gpt cover sig_s (P0) */
+  const double *sig_s2;     /* [n_mat][G_to][G_from] P2 moments, or NULL; order n adds to the source of
+                               direction l: sum_m Y_nm(Omega_l) sum_l' w_l' Y_nm(Omega_l') (sig_sn psi_l'),
+                               Y_nm the real spherical harmonics with unit mean square over the sphere */
+  const double *sig_s3;     /* [n_mat][G_to][G_from] P3 moments, or NULL */
 } tt_problem;
 
 typedef enum {

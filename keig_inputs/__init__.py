@@ -156,6 +156,8 @@ class Problem:
     rmax: int = 64
     inv_v: Optional[np.ndarray] = None
     sig_s1: Optional[np.ndarray] = None  # [m, g_to, g_from] P1 scattering moments (linear anisotropy)
+    sig_s2: Optional[np.ndarray] = None  # [m, g_to, g_from] P2 moments
+    sig_s3: Optional[np.ndarray] = None  # [m, g_to, g_from] P3 moments
 
     @property
     def n(self) -> int:
@@ -419,3 +421,12 @@ def with_linear_anisotropy(prob: Problem, mu_bar: float) -> Problem:
     keeps the P1 kernel 1 + 3 mu_bar cos non-negative)."""
     return dataclasses.replace(prob, sig_s1=mu_bar * np.asarray(prob.sig_s, dtype=np.float64),
                                name=prob.name + f"_p1_{mu_bar:g}")
+
+
+def with_anisotropy(prob: Problem, f1: float, f2: float = 0.0, f3: float = 0.0) -> Problem:
+    """The same problem with Legendre scattering moments sig_sn = f_n * sig_s
+    for n = 1..3 (f_n = 0 leaves the order out)."""
+    s0 = np.asarray(prob.sig_s, dtype=np.float64)
+    return dataclasses.replace(prob, sig_s1=f1 * s0 if f1 else None, sig_s2=f2 * s0 if f2 else None,
+                               sig_s3=f3 * s0 if f3 else None,
+                               name=prob.name + f"_aniso_{f1:g}_{f2:g}_{f3:g}")

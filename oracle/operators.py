@@ -79,6 +79,51 @@ def _oct_sel(o):
     return e
 
 
+def real_sh(n, m, x, y, z):
+    """Real spherical harmonic of degree n, order m (m > 0 cosine type, m < 0
+    sine type) with unit mean square over the sphere (Y_00 = 1), written out
+    as Cartesian polynomials for n <= 3 at the direction (x, y, z)."""
+    r3, r5, r7 = np.sqrt(3.0), np.sqrt(5.0), np.sqrt(7.0)
+    table = {
+        (0, 0): lambda: np.ones_like(np.asarray(x, dtype=np.float64)),
+        (1, 1): lambda: r3 * x, (1, -1): lambda: r3 * y, (1, 0): lambda: r3 * z,
+        (2, 0): lambda: r5 / 2 * (3 * z * z - 1), (2, 1): lambda: np.sqrt(15.0) * x * z,
+        (2, -1): lambda: np.sqrt(15.0) * y * z, (2, 2): lambda: np.sqrt(15.0) / 2 * (x * x - y * y),
+        (2, -2): lambda: np.sqrt(15.0) * x * y,
+        (3, 0): lambda: r7 / 2 * (5 * z ** 3 - 3 * z), (3, 1): lambda: np.sqrt(42.0) / 4 * x * (5 * z * z - 1),
+        (3, -1): lambda: np.sqrt(42.0) / 4 * y * (5 * z * z - 1),
+        (3, 2): lambda: np.sqrt(105.0) / 2 * z * (x * x - y * y), (3, -2): lambda: np.sqrt(105.0) * x * y * z,
+        (3, 3): lambda: np.sqrt(70.0) / 4 * x * (x * x - 3 * y * y),
+        (3, -3): lambda: np.sqrt(70.0) / 4 * y * (3 * x * x - y * y),
+    }
+    return table[(n, m)]()
+
+
+def signed_directions(q):
+    """(x, y, z) cosines of all L directions, octant-major (octant o has
+    positive x if o & 1, y if o & 2, z if o & 4)."""
+    m8 = q.n_per_octant
+    xs, ys, zs = [], [], []
+    for o in range(8):
+        xs.append(np.asarray(q.amu) * (1 if o & 1 else -1))
+        ys.append(np.asarray(q.aeta) * (1 if o & 2 else -1))
+        zs.append(np.asarray(q.axi) * (1 if o & 4 else -1))
+    return np.concatenate(xs), np.concatenate(ys), np.concatenate(zs)
+
+
+def aniso_angular(q, n):
+    """L x L angular matrix of the order-n scattering term: entry (l, l') =
+    sum_m Y_nm(Omega_l) Y_nm(Omega_l') w_l' (the moment operators
+    L_n^+ L_n of Appendix A.2 with weights summing to 1)."""
+    x, y, z = signed_directions(q)
+    w = np.tile(q.w8, 8)
+    A = np.zeros((x.size, x.size))
+    for m in range(-n, n + 1):
+        v = real_sh(n, m, x, y, z)
+        A += np.outer(v, v * w)
+    return A
+
+
 def assemble(prob):
     """Sparse H, S, F (the matrices of Eq. (OpFormkNTE)) for a small grid."""
     n, G = prob.n, prob.G
@@ -115,6 +160,15 @@ def assemble(prob):
             f_t = _kron(np.outer(prob.chi[m], prob.nu_sig_f[m]), intg, dirm, mask @ spat_nobc)
             S = s_t if S is None else S + s_t
             F = f_t if F is None else F + f_t
+            for nord, field in ((2, "sig_s2"), (3, "sig_s3")):
+                sn = getattr(prob, field, None)
+                if sn is not None:
+                    # order-n term: the L x L angular matrix restricted to the
+                    # rows of octant o, with the order-n group matrix
+                    A = aniso_angular(q, nord)
+                    rows = np.zeros_like(A)
+                    rows[o * m8:(o + 1) * m8, :] = A[o * m8:(o + 1) * m8, :]
+                    S = S + _kron(np.asarray(sn[m]), rows, mask @ spat_nobc)
             s1 = getattr(prob, "sig_s1", None)
             if s1 is not None:
                 # linear anisotropy (N_s = 1 of the moment operators, weights

@@ -106,6 +106,9 @@ class OracleProblem:
         for i in range(6):
             s.bc[i] = int(prob.bc[i])
         s.threads = int(threads)
+        if getattr(prob, "sig_s2", None) is not None or getattr(prob, "sig_s3", None) is not None:
+            raise NotImplementedError("the stencil oracle covers scattering orders N_s <= 1; use "
+                                      "operators.assemble and operators.ges_k for higher orders")
         if getattr(prob, "sig_s1", None) is not None:
             self._keep["sig_s1"] = np.ascontiguousarray(prob.sig_s1, dtype=np.float64)
             s.sig_s1 = _dp(self._keep["sig_s1"])

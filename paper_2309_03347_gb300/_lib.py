@@ -35,7 +35,8 @@ class TTProblem(C.Structure):
         ("l", C.c_int), ("side", C.c_double * 3), ("G", C.c_int), ("n_mat", C.c_int),
         ("sig_t", D), ("sig_s", D), ("nu_sig_f", D), ("chi", D), ("inv_v", D),
         ("mat", C.POINTER(C.c_uint8)), ("n_dir", C.c_int),
-        ("amu", D), ("aeta", D), ("axi", D), ("w", D), ("bc", C.c_int * 6), ("sig_s1", D),
+        ("amu", D), ("aeta", D), ("axi", D), ("w", D), ("bc", C.c_int * 6), ("sig_s1", D), ("sig_s2", D),
+        ("sig_s3", D),
     ]
 
 
@@ -409,11 +410,12 @@ class _ProblemArrays:
         s.amu, s.aeta, s.axi, s.w = _dp(a["amu"]), _dp(a["aeta"]), _dp(a["axi"]), _dp(a["w"])
         for i in range(6):
             s.bc[i] = int(prob.bc[i])
-        if getattr(prob, "sig_s1", None) is not None:
-            a["sig_s1"] = np.ascontiguousarray(prob.sig_s1, np.float64)
-            s.sig_s1 = _dp(a["sig_s1"])
-        else:
-            s.sig_s1 = None
+        for f in ("sig_s1", "sig_s2", "sig_s3"):
+            if getattr(prob, f, None) is not None:
+                a[f] = np.ascontiguousarray(getattr(prob, f), np.float64)
+                setattr(s, f, _dp(a[f]))
+            else:
+                setattr(s, f, None)
         self.s = s
 
 

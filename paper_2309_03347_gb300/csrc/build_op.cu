@@ -48,6 +48,40 @@ std::vector<double> factor_Ip(int n, bool pos, bool no_bc) {
   return a;
 }
 
+// Real spherical harmonic Y_nm (m > 0 cosine type, m < 0 sine type) with
+// unit mean square over the sphere, at the unit direction (x, y, z), z the
+// polar axis: sqrt((2n+1)(2 - delta_m0)(n-|m|)!/(n+|m|)!) P_n^|m|(z) trig(|m| phi),
+// P_n^m by the standard three-term recurrence in n (no Condon-Shortley phase).
+double real_sh(int n, int m, double x, double y, double z) {
+  const int am = m < 0 ? -m : m;
+  const double st = std::sqrt(std::max(0.0, 1.0 - z * z));
+  double pmm = 1.0;
+  for (int i = 1; i <= am; ++i) pmm *= (2.0 * i - 1.0) * st;
+  double P = pmm;
+  if (n > am) {
+    double a = pmm, b = z * (2.0 * am + 1.0) * pmm;
+    for (int ll = am + 2; ll <= n; ++ll) {
+      const double cnew = (z * (2.0 * ll - 1.0) * b - (ll + am - 1.0) * a) / (ll - am);
+      a = b;
+      b = cnew;
+    }
+    P = b;
+  }
+  double ratio = 1.0;  // (n-|m|)! / (n+|m|)!
+  for (int i = n - am + 1; i <= n + am; ++i) ratio /= i;
+  const double norm = std::sqrt((2.0 * n + 1.0) * (am == 0 ? 1.0 : 2.0) * ratio);
+  const double phi = std::atan2(y, x);
+  return norm * P * (m >= 0 ? std::cos(am * phi) : std::sin(am * phi));
+}
+
+// Parity of Y_nm in (x, y, z): Y(s_x x, s_y y, s_z z) = s_x^px s_y^py s_z^pz Y(x, y, z)
+void sh_parity(int n, int m, int &px, int &py, int &pz) {
+  const int am = m < 0 ? -m : m;
+  pz = (n - am) & 1;
+  px = m >= 0 ? (am & 1) : ((am - 1) & 1);
+  py = m >= 0 ? 0 : 1;
+}
+
 int row_cell(int v, bool pos, int n) {
   int c = pos ? v - 1 : v;
   return std::max(0, std::min(c, n - 2));
@@ -273,15 +307,49 @@ TT assemble_operator(Ctx *c, const tt_problem *p, const OpFactors &F, int kind, 
             g1[e] = 3.0 * p->sig_s1[(size_t)m * G * G + e];
             nz1 |= g1[e] != 0.0;
           }
-          if (!nz1) continue;
           const double *cosv[3] = {p->amu, p->aeta, p->axi};
-          for (int a = 0; a < 3; ++a) {
+          for (int a = 0; a < 3 && nz1; ++a) {
             std::vector<double> octm(64, 0.0), dirp((size_t)nd * nd);
             const double so = (o >> a) & 1 ? 1.0 : -1.0;
             for (int j = 0; j < 8; ++j) octm[o * 8 + j] = so * ((j >> a) & 1 ? 1.0 : -1.0);
             for (int x = 0; x < nd; ++x)
               for (int y = 0; y < nd; ++y) dirp[(size_t)x * nd + y] = cosv[a][x] * cosv[a][y] * p->w[y];
             terms.push_back({{g1, octm, dirp}, {F.iIpN[pz], F.iIpN[py], F.iIpN[px]}, mi});
+          }
+        }
+        if (kind == TT_OP_S) {
+          // orders 2 and 3: for each m, Y_nm factors into an octant sign pattern
+          // (its parity) times its value at the first-octant direction, so the
+          // angular factor (row octant o) is rank one:
+          //   (sign(o) sign(o')) (x) (Y_nm(d) Y_nm(d') w_d')
+          const double *sn_tab[2] = {p->sig_s2, p->sig_s3};
+          for (int nn = 2; nn <= 3; ++nn) {
+            const double *sn = sn_tab[nn - 2];
+            if (!sn) continue;
+            std::vector<double> gn((size_t)G * G);
+            bool nzn = false;
+            for (size_t e = 0; e < (size_t)G * G; ++e) {
+              gn[e] = sn[(size_t)m * G * G + e];
+              nzn |= gn[e] != 0.0;
+            }
+            if (!nzn) continue;
+            for (int mm = -nn; mm <= nn; ++mm) {
+              int qx, qy, qz;
+              sh_parity(nn, mm, qx, qy, qz);
+              auto sgn = [&](int oo) {
+                double sv = 1.0;
+                if (qx && !(oo & 1)) sv = -sv;
+                if (qy && !(oo & 2)) sv = -sv;
+                if (qz && !(oo & 4)) sv = -sv;
+                return sv;
+              };
+              std::vector<double> octm(64, 0.0), dirp((size_t)nd * nd), v(nd);
+              for (int j = 0; j < 8; ++j) octm[o * 8 + j] = sgn(o) * sgn(j);
+              for (int dd = 0; dd < nd; ++dd) v[dd] = real_sh(nn, mm, p->amu[dd], p->aeta[dd], p->axi[dd]);
+              for (int x = 0; x < nd; ++x)
+                for (int y = 0; y < nd; ++y) dirp[(size_t)x * nd + y] = v[x] * v[y] * p->w[y];
+              terms.push_back({{gn, octm, dirp}, {F.iIpN[pz], F.iIpN[py], F.iIpN[px]}, mi});
+            }
           }
         }
       }

@@ -98,6 +98,8 @@ void validate_problem(const tt_problem *p) {
   check_finite_host(p->axi, nd, "axi");
   check_finite_host(p->w, nd, "w");
   if (p->sig_s1) check_finite_host(p->sig_s1, nm * G * G, "sig_s1");
+  if (p->sig_s2) check_finite_host(p->sig_s2, nm * G * G, "sig_s2");
+  if (p->sig_s3) check_finite_host(p->sig_s3, nm * G * G, "sig_s3");
   const size_t nc = ((size_t)1 << p->l) - 1;
   for (size_t i = 0; i < nc * nc * nc; ++i)
     TT_REQUIRE(p->mat[i] < p->n_mat, "problem: material index out of range");

@@ -333,6 +333,24 @@ def test_keig_linear_anisotropy_matches_oracle(ctx, mu_bar):
     assert rel(res["phi"], ref["phi"]) < 1e-5
 
 
+def test_higher_order_scattering_matches_oracle(ctx):
+    # scattering orders 1-3: the TT S operator against the Kronecker assembly
+    # (real spherical harmonics of the oracle, evaluated at the signed
+    # directions), and the fixed point against the library eigensolve
+    import dataclasses
+    p = ki.with_anisotropy(
+        dataclasses.replace(ki.fissile_box(l=3, G=2, order=4, seed=1003, half_width=2), side=(3.0,) * 3),
+        0.2, 0.1, 0.05)
+    H, S, F = O.assemble(p)
+    A = K.tt_build_operator(ctx, p, 1, 1e-13)
+    x = ki.random_cores(p.tt_modes, [1] + [2] * (len(p.tt_modes) - 1) + [1], 45)
+    y = K.tt_matvec(ctx, A, _vec(ctx, x), 1.0, K.TT_MV_EXACT, -1.0)
+    assert rel(y.dense_cuda().cpu().numpy().ravel(), S @ R.full(x).ravel()) < 1e-11
+    k_ref, _ = O.ges_k(p, H, S, F)
+    res = _keig_full_rank(ctx, p, 200, prec=K.TT_FP32_REFINED)
+    assert abs(res["k"] - k_ref) / k_ref < 1e-6, (res["k"], k_ref)
+
+
 @pytest.mark.slow
 def test_keig_config0_vacuum(ctx):
     # dominance ratio 0.956: about 200 power iterations to 1e-7 in k

@@ -299,3 +299,44 @@ def test_linear_anisotropy_oracle():
     assert ks[0] > ks[1] > ks[2]
     k_iso = T.OracleProblem(p0).keig(tol_k=1e-13, max_iter=100000)["k"]
     assert abs(ks[1] - k_iso) < 1e-14 * k_iso
+
+
+def test_higher_order_scattering_oracle():
+    # orders 2-3 of the scattering expansion: the real spherical harmonics of
+    # the oracle are orthonormal (unit mean square) under an exact product
+    # rule, satisfy the addition theorem sum_m Y_nm Y_nm' = (2n+1) P_n, the
+    # generic order-1 matrix equals the P1 form checked against the stencil,
+    # and every order n >= 1 conserves particles (angular integral zero)
+    from numpy.polynomial import legendre as Lg
+    zt, wt = Lg.leggauss(12)
+    ph = np.arange(24) * (2 * np.pi / 24)
+    Z, P = np.meshgrid(zt, ph, indexing="ij")
+    W = np.outer(wt, np.full(24, 1.0 / 24)) / 2.0  # weights of the unit sphere average
+    X, Y = np.sqrt(1 - Z ** 2) * np.cos(P), np.sqrt(1 - Z ** 2) * np.sin(P)
+    idx = [(n, m) for n in range(4) for m in range(-n, n + 1)]
+    vals = {nm: O.real_sh(*nm, X, Y, Z) for nm in idx}
+    for a in idx:
+        for b in idx:
+            assert abs(np.sum(W * vals[a] * vals[b]) - (a == b)) < 1e-12, (a, b)
+    rng = np.random.default_rng(2)
+    u = rng.standard_normal((3, 50)); u /= np.linalg.norm(u, axis=0)
+    v = rng.standard_normal((3, 50)); v /= np.linalg.norm(v, axis=0)
+    for n in range(4):
+        s = sum(O.real_sh(n, m, *u) * O.real_sh(n, m, *v) for m in range(-n, n + 1))
+        assert np.abs(s - (2 * n + 1) * Lg.legval(np.sum(u * v, axis=0), [0] * n + [1])).max() < 1e-12
+    q = ki.level_symmetric(4)
+    x, y, z = O.signed_directions(q)
+    w = np.tile(q.w8, 8)
+    A1 = O.aniso_angular(q, 1)
+    assert np.abs(A1 - 3 * (np.outer(x, x * w) + np.outer(y, y * w) + np.outer(z, z * w))).max() < 1e-13
+    for n in (1, 2, 3):
+        assert np.abs(w @ O.aniso_angular(q, n)).max() < 1e-13, n
+    # the assembled S: an isotropic flux sees no order-2/3 source
+    import dataclasses
+    p0 = dataclasses.replace(ki.fissile_box(l=2, G=2, order=4, seed=1003, half_width=1), side=(2.0,) * 3)
+    p = ki.with_anisotropy(p0, 0.0, 0.15, 0.05)
+    _, S0, _ = O.assemble(p0)
+    _, S, _ = O.assemble(p)
+    iso = np.broadcast_to(rng.standard_normal((p.G, 1, p.n, p.n, p.n)), p.psi_shape).ravel()
+    assert np.abs(S @ iso - S0 @ iso).max() < 1e-12
+    assert np.abs((S - S0) @ rng.standard_normal(S.shape[0])).max() > 1e-3
