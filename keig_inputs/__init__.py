@@ -22,7 +22,9 @@ set, Appendix A.2; a level-symmetric set is an equally valid octant-symmetric
 set and is what the synthetic workloads ask for).  Levels follow the standard
 recursion ``mu_i^2 = mu_1^2 + (i-1) * 2 (1 - 3 mu_1^2) / (N - 2)`` with the
 published base cosines; the weight of each permutation class is fixed by
-exact integration of even moments of one direction cosine over an octant.
+exact integration of even moments of one direction cosine over an octant
+(S16, where those moments leave one degree of freedom, takes the tabulated
+point weights).
 """
 from __future__ import annotations
 
@@ -41,6 +43,17 @@ _LQN_MU1 = {
     10: 0.1893213,
     12: 0.1672126,
     16: 0.1389568,
+}
+
+# Point weights of the orders whose even-moment system of one cosine does not
+# fix them (S16: eight point classes, seven independent conditions), as
+# tabulated with the base cosines above (Lewis & Miller, Table 4-1; weights of
+# one octant summing to 1), keyed by the sorted level-index triple of the
+# class.  The tabulated set also satisfies the mixed moments
+# <mu^2 eta^2> = 1/15 and <mu^2 eta^2 xi^2> = 1/105.
+_LQN_POINT_WEIGHTS = {
+    16: {(0, 0, 7): 0.0489872, (0, 1, 6): 0.0413296, (0, 2, 5): 0.0212326, (0, 3, 4): 0.0256207,
+         (1, 1, 5): 0.0360486, (1, 2, 4): 0.0144589, (1, 3, 3): 0.0344958, (2, 2, 3): 0.0085179},
 }
 
 
@@ -118,8 +131,15 @@ def level_symmetric(order: int) -> Quadrature:
         for ci, cl in enumerate(classes):
             a[r, ci] = sum(levels[q[0]] ** (2 * p) for q in pts
                            if tuple(sorted(q)) == cl)
-    wc, *_ = np.linalg.lstsq(a, rhs, rcond=1e-12)
-    if np.max(np.abs(a @ wc - rhs)) > 1e-9 or np.min(wc) <= 0:
+    if order in _LQN_POINT_WEIGHTS:
+        wc = np.array([_LQN_POINT_WEIGHTS[order][cl] for cl in classes])
+        count = np.array([sum(1 for q in pts if tuple(sorted(q)) == cl) for cl in classes])
+        wc = wc / float(count @ wc)  # the 7-digit table sums to 1 within 1e-6
+        tol = 1e-6
+    else:
+        wc, *_ = np.linalg.lstsq(a, rhs, rcond=1e-12)
+        tol = 1e-9
+    if np.max(np.abs(a @ wc - rhs)) > tol or np.min(wc) <= 0:
         raise ValueError(f"S{order}: moment system has no positive solution")
     cls_w = {cl: wc[i] for i, cl in enumerate(classes)}
     amu = np.array([levels[p[0]] for p in pts])

@@ -77,6 +77,14 @@ def test_quadrature_tables():
         assert abs(np.sum(q.w * q.mu ** 2) - 1 / 3) < 1e-6
         assert abs(np.sum(q.w * q.mu ** 4) - 1 / 5) < 1e-6
         assert abs(np.sum(q.w * q.mu)) < 1e-12
+        # every even moment of one cosine up to degree N, and the mixed
+        # moments an LQ_N set of order >= 6 integrates (the weights of S16
+        # are not fixed by the single-cosine conditions; the table's are)
+        for k in range(order // 2 + 1):
+            assert abs(np.sum(q.w * q.mu ** (2 * k)) - 1 / (2 * k + 1)) < 1e-7
+        if order >= 6:
+            assert abs(np.sum(q.w * q.mu ** 2 * q.eta ** 2) - 1 / 15) < 1e-7
+            assert abs(np.sum(q.w * q.mu ** 2 * q.eta ** 2 * q.xi ** 2) - 1 / 105) < 1e-7
 
 
 @pytest.mark.parametrize("hetero", [False, True])
@@ -109,6 +117,28 @@ def test_power_iteration_matches_ges(hetero):
     assert abs(r["k"] - kg) < 1e-10 * kg
     psi = r["psi"].ravel()
     assert np.linalg.norm(psi - v) < 1e-6 * np.linalg.norm(v)
+
+
+def test_mirror_rows_make_H_singular():
+    """Config 0 with every face reflective: replacing the inflow rows of H by
+    the mirror condition (the reading of reflective faces for the vertex
+    diamond difference; the paper treats vacuum faces only) gives a singular
+    H, so the fixed point of Eq. (k_eff_fixed_points), which applies H^{-1},
+    is undefined there.  Inverse iteration with a library LU finds a unit
+    vector in the numerical null space; the vacuum H is well conditioned."""
+    p = ki.config(0, "reflective")
+    H, _, _ = O.assemble(p)
+    Hr = O.reflective_rows(p, H)
+    x = np.random.default_rng(0).standard_normal(H.shape[0])
+    lu = spla.splu(Hr.tocsc())
+    for _ in range(3):
+        x = lu.solve(x)
+        x /= np.linalg.norm(x)
+    assert np.linalg.norm(Hr @ x) < 1e-12
+    assert np.linalg.norm(H @ x) > 1e-3
+    b = np.random.default_rng(1).standard_normal(H.shape[0])
+    xv = spla.splu(H.tocsc()).solve(b)
+    assert np.linalg.norm(xv) < 1e3 * np.linalg.norm(b)
 
 
 def test_infinite_medium_closed_form():
