@@ -58,9 +58,24 @@ typedef struct tt_op tt_op;
 
 /* ---------------------------------------------------------------- context */
 
+/* Device allocator supplied by the caller (e.g. a framework's caching
+ * allocator): alloc returns `bytes` of device memory usable on `cuda_stream`
+ * (aligned to at least 256 bytes) or NULL when it cannot; free returns a
+ * block obtained from alloc once the library's work on `cuda_stream` that
+ * uses it has been enqueued (stream-ordered reuse).  `user` is passed back
+ * unchanged.  Both are called only from the host thread that calls the
+ * library. */
+typedef void *(*tt_alloc_fn)(size_t bytes, void *cuda_stream, void *user);
+typedef void (*tt_free_fn)(void *ptr, void *cuda_stream, void *user);
+
 /* Create a context bound to the current CUDA device and to `cuda_stream`
- * (a cudaStream_t; NULL = the legacy default stream).  out: new handle. */
-int tt_ctx_create(tt_ctx **out, void *cuda_stream);
+ * (a cudaStream_t; NULL = the legacy default stream).  alloc_fn / free_fn:
+ * the device allocator for every buffer the context makes (both NULL: the
+ * device's stream-ordered pool, with freed blocks kept in the pool; exactly
+ * one NULL is TT_EINVAL).  When alloc_fn returns NULL the running call fails
+ * with TT_ENOMEM, frees what it allocated, and the context stays usable.
+ * out: new handle. */
+int tt_ctx_create(tt_ctx **out, void *cuda_stream, tt_alloc_fn alloc_fn, tt_free_fn free_fn, void *user);
 int tt_ctx_destroy(tt_ctx *ctx);
 const char *tt_last_error(const tt_ctx *ctx);
 /* Library version string (static storage). */
@@ -71,6 +86,13 @@ const char *tt_version(void);
  * updates), in FP64 and, for the mixed-precision solves, FP32 together. */
 int tt_ctx_counters(tt_ctx *ctx, int64_t *launches, double *contraction_flops);
 int tt_ctx_reset_counters(tt_ctx *ctx);
+/* Spin limit of the library's bounded device waits (the grid barriers of the
+ * persistent GMRES kernel): a CTA that has waited `spins` polls gives up,
+ * records TT_ETIMEOUT and returns, every other CTA of the launch returns at
+ * its next barrier, and the call fails with TT_ETIMEOUT; the context stays
+ * usable.  spins < 0 restores the default (2^24 polls of about 40 ns).  Small
+ * values make the waits run out: that is how the failure path is tested. */
+int tt_ctx_set_wait_limit(tt_ctx *ctx, long long spins);
 /* Per-launch timing of the dense contraction kernel (the FP64 GEMM that all
  * core contractions run on): when enabled, every launch is bracketed by CUDA
  * events on the context stream.  tt_ctx_gemm_stats synchronises and returns
@@ -88,6 +110,14 @@ int tt_ctx_gemmtc_stats(tt_ctx *ctx, int64_t *launches, double *ms, double *flop
  * solves (one launch per correction solve); flops = the local matvecs at
  * 2 n r0 r1 (r0 R1 + n R1 R2 + r1 R2) each plus the Gram-Schmidt passes. */
 int tt_ctx_gmres_stats(tt_ctx *ctx, int64_t *launches, double *ms, double *flops);
+
+/* Peak fused-multiply-add rate of the current device in flop/s (FP64 when
+ * fp64 != 0, else FP32): four CTAs of 256 threads per SM each run eight
+ * independent FMA chains for 16 x iters rounds; the best of `reps` timed
+ * launches (CUDA events on cuda_stream) after one warm-up.  The roofline
+ * denominator of the FP64 and FP32 SIMT kernels; the paper has no
+ * counterpart. */
+int tt_measure_fma_peak(void *cuda_stream, int fp64, int iters, int reps, double *flops_per_s);
 
 /* ---------------------------------------------------------------- TT vectors */
 
@@ -406,8 +436,9 @@ int tt_scalar_flux(tt_ctx *ctx, const tt_vec *psi, const double *w_host, int n_d
 
 /* <x, y> of two TT vectors without allocating device memory.  The paper has
  * no counterpart: this is a service for callers that cannot allocate at the
- * point of use (inside a CUDA-graph capture, in a real-time loop where an
- * allocation would stall the device, or under a fixed memory budget).
+ * point of use (a host that gives the library a fixed memory budget, or a
+ * real-time loop where cudaMalloc/cudaFree would stall or serialise the
+ * device).
  *
  * x_cores, y_cores: device pointers to all cores of x and y back to back,
  * core 0 first, each core (r_k, n_k, r_{k+1}) row-major (the layout of
@@ -419,8 +450,9 @@ int tt_scalar_flux(tt_ctx *ctx, const tt_vec *psi, const double *w_host, int n_d
  *
  * Scratch lives in one fixed 8.25 MiB device array that every GPU loading the
  * library holds until the process exits; the call never allocates.  The first
- * call on each device looks up that array's device address (no allocation),
- * so make it once before capturing a stream into a CUDA graph.  All calls
+ * call on each device looks up that array's device address (no allocation)
+ * and keeps it for the process, so make that first call before any stream
+ * capture; a cudaDeviceReset() invalidates the kept address.  All calls
  * share the array: calls that overlap on the GPU race and must be serialised
  * by the caller (one stream, or events).  Sizes above the limits return
  * TT_EINVAL before any work is enqueued. */

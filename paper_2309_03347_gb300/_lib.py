@@ -22,6 +22,9 @@ _lib = None
 
 D = C.POINTER(C.c_double)
 I = C.POINTER(C.c_int)
+# keig.h: tt_alloc_fn / tt_free_fn
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
 
 
 class KeigError(RuntimeError):
@@ -71,12 +74,14 @@ def load():
         lib = C.CDLL(_LIB_FILE)
         P = C.c_void_p
         sig = {
-            "tt_ctx_create": ([C.POINTER(P), P], C.c_int),
+            "tt_ctx_create": ([C.POINTER(P), P, ALLOC_FN, FREE_FN, P], C.c_int),
             "tt_ctx_destroy": ([P], C.c_int),
             "tt_last_error": ([P], C.c_char_p),
             "tt_version": ([], C.c_char_p),
             "tt_ctx_counters": ([P, C.POINTER(C.c_int64), D], C.c_int),
             "tt_ctx_reset_counters": ([P], C.c_int),
+            "tt_ctx_set_wait_limit": ([P, C.c_longlong], C.c_int),
+            "tt_measure_fma_peak": ([P, C.c_int, C.c_int, C.c_int, D], C.c_int),
             "tt_ctx_set_profiling": ([P, C.c_int], C.c_int),
             "tt_ctx_gemm_stats": ([P, C.POINTER(C.c_int64), D, D], C.c_int),
             "tt_ctx_gemm32_stats": ([P, C.POINTER(C.c_int64), D, D], C.c_int),
@@ -127,10 +132,34 @@ def _ip(a):
     return a, a.ctypes.data_as(I)
 
 
-class Context:
-    """A tt_ctx bound to the current CUDA device and a torch CUDA stream."""
+class TorchCachingAllocator:
+    """Device allocator hooks (keig.h tt_alloc_fn / tt_free_fn) that draw on
+    PyTorch's caching allocator, so the library shares torch's memory pool.
+    alloc(bytes, stream) returns a device address or 0; free(ptr, stream)."""
 
-    def __init__(self, stream=None):
+    def __init__(self, device=None):
+        import torch
+        self.device = torch.cuda.current_device() if device is None else int(device)
+
+    def alloc(self, nbytes: int, stream: int) -> int:
+        import torch
+        try:
+            return int(torch.cuda.caching_allocator_alloc(int(nbytes), self.device, stream))
+        except RuntimeError:  # out of memory
+            return 0
+
+    def free(self, ptr: int, stream: int) -> None:
+        import torch
+        torch.cuda.caching_allocator_delete(ptr)
+
+
+class Context:
+    """A tt_ctx bound to the current CUDA device and a torch CUDA stream.
+    allocator: None (the device's stream-ordered pool) or an object with
+    alloc(nbytes, stream) -> address (0 on failure) and free(address, stream),
+    e.g. TorchCachingAllocator()."""
+
+    def __init__(self, stream=None, allocator=None):
         import torch
         if not torch.cuda.is_available():
             raise KeigError(TT_ECUDA, "CUDA device required (no CPU fallback)")
@@ -138,8 +167,20 @@ class Context:
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
+        self.allocator = allocator
+        if allocator is not None:
+            def _alloc(nbytes, strm, user):
+                return allocator.alloc(nbytes, strm or 0) or None
+
+            def _free(ptr, strm, user):
+                allocator.free(ptr, strm or 0)
+            # the callbacks must outlive the context
+            self._hooks = (ALLOC_FN(_alloc), FREE_FN(_free))
+        else:
+            self._hooks = (ALLOC_FN(), FREE_FN())
         h = C.c_void_p()
-        self._check(self.lib.tt_ctx_create(C.byref(h), C.c_void_p(stream.cuda_stream)), None)
+        self._check(self.lib.tt_ctx_create(C.byref(h), C.c_void_p(stream.cuda_stream), self._hooks[0],
+                                           self._hooks[1], None), None)
         self.h = h
 
     def _check(self, rc, h="self"):
@@ -170,6 +211,10 @@ class Context:
 
     def reset_counters(self):
         self.check(self.lib.tt_ctx_reset_counters(self.h))
+
+    def set_wait_limit(self, spins: int):
+        """Spin limit of the bounded device waits (keig.h); < 0: default."""
+        self.check(self.lib.tt_ctx_set_wait_limit(self.h, int(spins)))
 
     def set_profiling(self, on: bool):
         self.check(self.lib.tt_ctx_set_profiling(self.h, int(bool(on))))
@@ -308,8 +353,8 @@ class TTOp:
 
 # ---------------------------------------------------------------- C-ABI names
 
-def tt_ctx_create(stream=None) -> Context:
-    return Context(stream)
+def tt_ctx_create(stream=None, allocator=None) -> Context:
+    return Context(stream, allocator)
 
 
 def _cat(cores: Sequence):
@@ -520,15 +565,32 @@ def tt_scalar_flux(ctx: Context, psi: TTVec, w8) -> TTVec:
 
 def tt_dot_noalloc(x_cores, rx, y_cores, ry, n, out, stream=None) -> None:
     """<x, y> into the one-element CUDA tensor `out`, for callers that cannot
-    allocate device memory where they need the product (graph capture,
-    fixed memory budgets).  x_cores / y_cores: contiguous float64 CUDA tensors
-    holding all cores back to back; rx, ry, n: ranks and modes (host ints).
-    The library allocates nothing; see keig.h for the shared-scratch rules."""
+    allocate device memory where they need the product (a fixed memory
+    budget, or a loop where an allocation would stall the device).
+    x_cores / y_cores: contiguous float64 CUDA tensors holding all cores back
+    to back; rx, ry, n: ranks and modes (host ints).  The sizes are checked
+    against the tensors before the call; the library allocates nothing and
+    shares one scratch array between all calls (keig.h)."""
     import torch
     lib = load()
+    n = [int(v) for v in n]
+    rx = [int(v) for v in rx]
+    ry = [int(v) for v in ry]
+    d = len(n)
+    if d < 1 or len(rx) != d + 1 or len(ry) != d + 1:
+        raise KeigError(TT_EINVAL, "tt_dot_noalloc: rx and ry need len(n) + 1 entries")
+    if min(n + rx + ry) < 1:
+        raise KeigError(TT_EINVAL, "tt_dot_noalloc: ranks and modes must be positive")
     for t in (x_cores, y_cores, out):
         if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
             raise KeigError(TT_EINVAL, "tt_dot_noalloc: expects contiguous float64 CUDA tensors")
+    for name, t, r in (("x_cores", x_cores, rx), ("y_cores", y_cores, ry)):
+        need = sum(r[k] * n[k] * r[k + 1] for k in range(d))
+        if t.numel() != need:
+            raise KeigError(TT_EINVAL, f"tt_dot_noalloc: {name} holds {t.numel()} doubles, the ranks and "
+                                       f"modes need {need}")
+    if out.numel() < 1:
+        raise KeigError(TT_EINVAL, "tt_dot_noalloc: out needs one element")
     if stream is None:
         stream = torch.cuda.current_stream()
     rxa, rxp = _ip(rx)
@@ -688,3 +750,50 @@ def keig_k_function():
             return gk * gt, gk * gs, gk * gn, gk * gc, None, None, None
 
     return KeigK
+
+
+def keig_j_function():
+    """A torch.autograd.Function computing the flux functional
+    J = sum_g sum_v resp_g[g] resp_v[v] phi[g, v] of the production-normalised
+    eigenvector from the cross-section tables (sig_t, sig_s, nu_sig_f, chi) of
+    a problem template; its backward uses the GPT gradients that keig_gpt
+    returns with J (one adjoint fixed point and one fixed-source iteration in
+    the forward call)."""
+    import dataclasses
+
+    import torch
+
+    class KeigJ(torch.autograd.Function):
+        @staticmethod
+        def forward(fctx, sig_t, sig_s, nu_sig_f, chi, problem, resp_g, resp_v, ctx, opts, tol_gpt=1e-8,
+                    max_gpt=500):
+            p = dataclasses.replace(problem, sig_t=sig_t.detach().cpu().double().numpy(),
+                                    sig_s=sig_s.detach().cpu().double().numpy(),
+                                    nu_sig_f=nu_sig_f.detach().cpu().double().numpy(),
+                                    chi=chi.detach().cpu().double().numpy())
+            r = keig_gpt(ctx, p, resp_g, resp_v, opts, tol_gpt=tol_gpt, max_gpt=max_gpt)
+            grads = [torch.from_numpy(r[f]).to(sig_t.device, sig_t.dtype)
+                     for f in ("sig_t", "sig_s", "nu_sig_f", "chi")]
+            fctx.save_for_backward(*grads)
+            return torch.tensor(r["J"], dtype=sig_t.dtype, device=sig_t.device)
+
+        @staticmethod
+        def backward(fctx, gj):
+            gt, gs, gn, gc = fctx.saved_tensors
+            return gj * gt, gj * gs, gj * gn, gj * gc, None, None, None, None, None, None, None
+
+    return KeigJ
+
+
+def tt_measure_fma_peak(fp64: bool, iters: int = 4096, reps: int = 5, stream=None) -> float:
+    """Peak FMA rate of the current device in flop/s (keig.h)."""
+    import torch
+    lib = load()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    out = C.c_double()
+    rc = lib.tt_measure_fma_peak(C.c_void_p(stream.cuda_stream), int(bool(fp64)), int(iters), int(reps),
+                                 C.byref(out))
+    if rc != TT_OK:
+        raise KeigError(rc, "tt_measure_fma_peak failed")
+    return float(out.value)

@@ -12,7 +12,7 @@ SRC_DIR = os.path.join(HERE, "csrc")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD_DIR, "libkeig_tt.so")
 SOURCES = ["kernels.cu", "ttcore.cu", "amen.cu", "build_op.cu", "capi.cu", "noalloc.cu", "svd_mixed.cu",
-           "tc_gemm.cu", "krylov.cu", "pgmres.cu"]
+           "tc_gemm.cu", "krylov.cu", "pgmres.cu", "peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]

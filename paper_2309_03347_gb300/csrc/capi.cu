@@ -111,9 +111,10 @@ extern "C" {
 
 const char *tt_version(void) { return "keig-tt 0.1 (sm_103a, FP64)"; }
 
-int tt_ctx_create(tt_ctx **out, void *stream) {
+int tt_ctx_create(tt_ctx **out, void *stream, tt_alloc_fn alloc_fn, tt_free_fn free_fn, void *user) {
   if (!out) return TT_EINVAL;
   *out = nullptr;
+  if ((alloc_fn == nullptr) != (free_fn == nullptr)) return TT_EINVAL;
   tt_ctx *ctx = new (std::nothrow) tt_ctx();
   if (!ctx) return TT_ENOMEM;
   int rc = guarded(ctx, [&] {
@@ -125,6 +126,9 @@ int tt_ctx_create(tt_ctx **out, void *stream) {
     TT_CHECK_CUDA(cudaGetDeviceProperties(&prop, ctx->c.device));
     ctx->c.sm_count = prop.multiProcessorCount;
     ctx->c.stream = (cudaStream_t)stream;
+    ctx->c.alloc_fn = alloc_fn;
+    ctx->c.free_fn = free_fn;
+    ctx->c.alloc_user = user;
     ctx->c.phase_timing = getenv("KEIG_PHASE_TIMES") != nullptr;
     ctx->c.mixed_svd = getenv("KEIG_FP64_SVD") == nullptr;
     ctx->c.persistent_gmres = getenv("KEIG_LAUNCHED_GMRES") == nullptr;
@@ -133,8 +137,9 @@ int tt_ctx_create(tt_ctx **out, void *stream) {
     TT_CHECK_CUDA(cudaDeviceGetDefaultMemPool(&pool, ctx->c.device));
     uint64_t thr = UINT64_MAX;
     TT_CHECK_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
-    TT_CHECK_CUDA(cudaMalloc(&ctx->c.d_scalar, 64 * sizeof(double)));
-    TT_CHECK_CUDA(cudaMemset(ctx->c.d_scalar, 0, 64 * sizeof(double)));
+    ctx->c.scalar_buf.alloc(&ctx->c, 64);
+    ctx->c.d_scalar = ctx->c.scalar_buf.p();
+    TT_CHECK_CUDA(cudaMemsetAsync(ctx->c.d_scalar, 0, 64 * sizeof(double), ctx->c.stream));
     TT_CHECK_CUDA(cudaMallocHost(&ctx->c.h_pinned, 4096 * sizeof(double)));
   });
   if (rc != TT_OK) {
@@ -153,7 +158,8 @@ int tt_ctx_destroy(tt_ctx *ctx) {
   ctx->c.ws_tc.release();
   for (auto &s : ctx->c.scratch) s.release();
   cudaStreamSynchronize(ctx->c.stream);
-  if (ctx->c.d_scalar) cudaFree(ctx->c.d_scalar);
+  ctx->c.scalar_buf.release();
+  cudaStreamSynchronize(ctx->c.stream);
   if (ctx->c.h_pinned) cudaFreeHost(ctx->c.h_pinned);
   for (auto &e : ctx->c.ev_pool) {
     cudaEventDestroy(e.first);
@@ -169,6 +175,12 @@ int tt_ctx_counters(tt_ctx *ctx, int64_t *launches, double *flops) {
   if (!ctx) return TT_EINVAL;
   if (launches) *launches = ctx->c.launches;
   if (flops) *flops = ctx->c.flops + ctx->c.flops32;
+  return TT_OK;
+}
+
+int tt_ctx_set_wait_limit(tt_ctx *ctx, long long spins) {
+  if (!ctx) return TT_EINVAL;
+  ctx->c.wait_limit = spins < 0 ? -1 : spins;
   return TT_OK;
 }
 

@@ -81,15 +81,22 @@ class DBuf {
 struct Ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
+  // caller-supplied device allocator (tt_ctx_create); null: the stream-ordered pool
+  tt_alloc_fn alloc_fn = nullptr;
+  tt_free_fn free_fn = nullptr;
+  void *alloc_user = nullptr;
   std::string err;
   int64_t launches = 0;
   double flops = 0.0;    // algorithmic contraction flops (FP64)
   double flops32 = 0.0;  // algorithmic contraction flops run in FP32
   int sm_count = 152;
+  // spin limit of the bounded device waits (grid barriers); < 0: the kernels' defaults
+  long long wait_limit = -1;
   // scratch buffers reused across calls (grown on demand)
   DBuf ws_gemm;    // split-K partial sums (FP64)
   DBuf ws_gemm32;  // split-K partial sums (FP32, stored in a double-typed buffer)
   DBuf scratch[8];
+  DBuf scalar_buf;             // owns d_scalar
   double *d_scalar = nullptr;  // small device area for reductions (64 doubles)
   // optional per-launch timing of the contraction GEMMs (CUDA events)
   bool profiling = false;

@@ -14,16 +14,26 @@ void DBuf::alloc(Ctx *c, size_t n) {
   ctx_ = c;
   if (n == 0) n = 1;
   void *p = nullptr;
-  cudaError_t e = cudaMallocAsync(&p, n * sizeof(double), c->stream);
-  if (e != cudaSuccess)
-    throw Error(e == cudaErrorMemoryAllocation ? TT_ENOMEM : TT_ECUDA,
-                std::string("cudaMallocAsync(") + std::to_string(n * 8) + "): " + cudaGetErrorString(e));
+  if (c->alloc_fn) {
+    p = c->alloc_fn(n * sizeof(double), (void *)c->stream, c->alloc_user);
+    if (!p) throw Error(TT_ENOMEM, "caller allocator returned NULL for " + std::to_string(n * 8) + " bytes");
+  } else {
+    cudaError_t e = cudaMallocAsync(&p, n * sizeof(double), c->stream);
+    if (e != cudaSuccess)
+      throw Error(e == cudaErrorMemoryAllocation ? TT_ENOMEM : TT_ECUDA,
+                  std::string("cudaMallocAsync(") + std::to_string(n * 8) + "): " + cudaGetErrorString(e));
+  }
   p_ = static_cast<double *>(p);
   n_ = cap_ = n;
 }
 
 void DBuf::release() {
-  if (p_ && ctx_) cudaFreeAsync(p_, ctx_->stream);
+  if (p_ && ctx_) {
+    if (ctx_->free_fn)
+      ctx_->free_fn(p_, (void *)ctx_->stream, ctx_->alloc_user);
+    else
+      cudaFreeAsync(p_, ctx_->stream);
+  }
   p_ = nullptr;
   n_ = cap_ = 0;
 }

@@ -1,10 +1,9 @@
 // Allocation-free inner product of two TT vectors (tt_dot_noalloc).
 //
 // Some callers cannot allocate device memory at the point where they need
-// the result: code running inside a CUDA-graph capture or a real-time loop
-// where cudaMalloc/cudaFree would stall or serialise the device, and hosts
-// that hand the library a fixed memory budget and forbid further
-// allocations.  For them this entry point computes <x, y> with its scratch in
+// the result: a real-time loop where cudaMalloc/cudaFree would stall or
+// serialise the device, and hosts that hand the library a fixed memory
+// budget and forbid further allocations.  For them this entry point computes <x, y> with its scratch in
 // a fixed file-scope device array instead of the context's allocator.
 //
 // The scratch array lives in every device that loads the library until the
@@ -94,7 +93,8 @@ extern "C" int tt_dot_noalloc(const double *x_cores, const int *rx, const double
   }
   double *scratch = nullptr;
   {
-    // first call on a device: look up the device address of the array
+    // first call on a device: look up the device address of the array (kept
+    // for the process; a cudaDeviceReset invalidates it)
     std::lock_guard<std::mutex> lock(g_mu);
     if (!g_scratch_addr[dev]) {
       void *p = nullptr;

@@ -35,6 +35,7 @@ struct PGArgs {
   unsigned *bar;   // [0] arrivals, [1] generation
   int r0, R1, m, R2, r1, N, mr, maxit, split3, kchunk3, chunk, gv;
   double tol;
+  long long bar_limit;  // spins of a CTA waiting at the grid barrier before it gives up
 };
 
 // offsets into the device state D (doubles) for restart mr and G CTAs
@@ -64,7 +65,7 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 }
 
 // Grid barrier over co-resident CTAs (cooperative launch); bounded spin.
-__device__ bool grid_sync(unsigned *bar, int *err) {
+__device__ bool grid_sync(unsigned *bar, int *err, long long limit) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -79,7 +80,7 @@ __device__ bool grid_sync(unsigned *bar, int *err) {
     } else {
       long long spins = 0;
       while (*vgen == g) {
-        if (++spins > BAR_LIMIT) {
+        if (++spins > limit) {
           ok = 0;
           atomicExch(err, TT_ETIMEOUT);
           break;
@@ -195,10 +196,10 @@ __device__ bool matvec_tail(const PGArgs &P, float (*As)[TBM + 1], float (*Bs)[T
   const int r0 = P.r0, R1 = P.R1, m = P.m, R2 = P.R2, r1 = P.r1;
   gemm_phase<true, false>(m * R2, r1, R1 * m, 1.f, P.A, m * R2, 0, P.T1, r1, (long long)R1 * m * r1, P.T2, r1,
                           (long long)m * R2 * r1, r0, 1, R1 * m, 0, As, Bs);
-  if (!grid_sync(P.bar, P.st + 1)) return false;
+  if (!grid_sync(P.bar, P.st + 1, P.bar_limit)) return false;
   gemm_phase<false, true>(r0 * m, r1, R2 * r1, 1.f, P.T2, R2 * r1, 0, P.PR, R2 * r1, 0, P.ws, r1, 0, 1, P.split3,
                           P.kchunk3, (long long)P.N, As, Bs);
-  return grid_sync(P.bar, P.st + 1);
+  return grid_sync(P.bar, P.st + 1, P.bar_limit);
 }
 
 // w-partials of the matvec of v (scale alpha) into ws (split3 slices of N)
@@ -207,7 +208,7 @@ __device__ bool matvec_phases(const PGArgs &P, const float *v, float alpha, floa
   const int r0 = P.r0, R1 = P.R1, m = P.m, r1 = P.r1;
   gemm_phase<false, false>(r0 * R1, m * r1, r0, alpha, P.PL, r0, 0, v, m * r1, 0, P.T1, m * r1, 0, 1, 1, r0, 0, As,
                            Bs);
-  if (!grid_sync(P.bar, P.st + 1)) return false;
+  if (!grid_sync(P.bar, P.st + 1, P.bar_limit)) return false;
   return matvec_tail(P, As, Bs);
 }
 
@@ -342,7 +343,7 @@ __global__ void __launch_bounds__(PG_THREADS, 1) pgmres_kernel(PGArgs P) {
       if (tid == 0 && bid < Gv) D[L.npart + bid] = sq;
     }
     first = false;
-    if (!grid_sync(P.bar, err)) return;
+    if (!grid_sync(P.bar, err, P.bar_limit)) return;
     {
       const double beta = norm_from_partials();
       if (tid == 0) {
@@ -369,7 +370,7 @@ __global__ void __launch_bounds__(PG_THREADS, 1) pgmres_kernel(PGArgs P) {
         ++steps;
       }
       if (j == mr) {
-        if (!grid_sync(P.bar, err)) return;
+        if (!grid_sync(P.bar, err, P.bar_limit)) return;
         break;
       }
       // T1 = Phi_L (s_j V_j), then the flags of step j - 1 are visible
@@ -377,7 +378,7 @@ __global__ void __launch_bounds__(PG_THREADS, 1) pgmres_kernel(PGArgs P) {
         const int r0 = P.r0, R1 = P.R1, m = P.m, r1 = P.r1;
         gemm_phase<false, false>(r0 * R1, m * r1, r0, (float)ss[j], P.PL, r0, 0, P.V + (size_t)j * N, m * r1, 0,
                                  P.T1, m * r1, 0, 1, 1, r0, 0, As, Bs);
-        if (!grid_sync(P.bar, err)) return;
+        if (!grid_sync(P.bar, err, P.bar_limit)) return;
       }
       if (j > 0 && __ldcg(P.st + 2)) {
         jend = j - 1;
@@ -401,7 +402,7 @@ __global__ void __launch_bounds__(PG_THREADS, 1) pgmres_kernel(PGArgs P) {
       }
       __syncthreads();
       inner(D + L.part, j);
-      if (!grid_sync(P.bar, err)) return;
+      if (!grid_sync(P.bar, err, P.bar_limit)) return;
       // two subtraction passes; the second also forms the norm partials and stores w
       for (int pass = 0; pass < 2; ++pass) {
         const double *part = D + (pass == 0 ? L.part : L.part2);
@@ -428,7 +429,7 @@ __global__ void __launch_bounds__(PG_THREADS, 1) pgmres_kernel(PGArgs P) {
           sq = block_total(sq);
           if (tid == 0 && bid < Gv) D[L.npart + bid] = sq;
         }
-        if (!grid_sync(P.bar, err)) return;
+        if (!grid_sync(P.bar, err, P.bar_limit)) return;
       }
     }
     // ---- x += sum_v y_v s_v V_v with y = H^-1 g over the columns 0..jend
@@ -443,11 +444,11 @@ __global__ void __launch_bounds__(PG_THREADS, 1) pgmres_kernel(PGArgs P) {
       }
       for (int i = 0; i < kk; ++i) y[i] *= ss[i];
     }
-    if (!grid_sync(P.bar, err)) return;
+    if (!grid_sync(P.bar, err, P.bar_limit)) return;
     for (int v = tid; v <= jend; v += PG_THREADS) hsc[v] = (float)__ldcg(D + L.y + v);
     __syncthreads();
     for (int i = tid; i < cn; i += PG_THREADS) P.x[lo + i] += sub_comb(i, jend);
-    if (!grid_sync(P.bar, err)) return;
+    if (!grid_sync(P.bar, err, P.bar_limit)) return;
     if (__ldcg(P.st + 3)) break;
   }
 }
@@ -511,6 +512,7 @@ int pgmres32(Ctx *c, const float *PL, const float *A32, const float *PR, int r0,
   P.chunk = chunk;
   P.gv = gv;
   P.tol = tol;
+  P.bar_limit = c->wait_limit >= 0 ? c->wait_limit : BAR_LIMIT;
   void *args[] = {&P};
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   if (c->profiling) {

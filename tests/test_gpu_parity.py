@@ -385,10 +385,13 @@ def test_adjoint_sensitivities_match_finite_differences(ctx, case):
     g = K.keig_sensitivities(ctx, p, o)
     assert abs(g["k"] - g["k_adjoint"]) < 1e-8 * g["k"]
     fd = SE.fd_gradients(p)
+    # per entry: 1e-4 relative to that entry's finite difference, with an
+    # absolute floor of 1e-7 x the largest derivative for the finite
+    # difference's own noise (k converged to 1e-13, step 1e-6 relative)
     scale = max(np.abs(v).max() for v in fd.values())
     for f in SE.FIELDS:
-        err = np.abs(g[f] - fd[f]).max() / scale
-        assert err < 1e-4, (f, err, g[f], fd[f])
+        bad = np.abs(g[f] - fd[f]) > 1e-4 * np.abs(fd[f]) + 1e-7 * scale
+        assert not bad.any(), (f, g[f][bad], fd[f][bad])
 
 
 def test_autograd_function_backward(ctx):
