@@ -150,13 +150,24 @@ def first_within(k_hist, t_hist, k_ref, tol=1e-6):
     return None, None
 
 
+def cpu_model():
+    """The host CPU's model name (from /proc/cpuinfo; 'unknown' if absent)."""
+    try:
+        for line in open("/proc/cpuinfo"):
+            key = line.split(":")[0].strip().lower()
+            if key in ("model name", "cpu part", "hardware"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine() or "unknown"
+
+
 def run_reference(args, p):
-    """The oracle (plain FP64 CPU power iteration) on the same workload."""
-    import multiprocessing as mp
+    """The oracle (plain FP64 CPU power iteration) on the same workload; the
+    CPU program keeps no state between runs, so it needs no warm-up."""
     cores = os.cpu_count() or 1
     times, kref = [], None
-    for _ in range(args.warmup):
-        pass  # the CPU program has no warm-up state
     for _ in range(args.steps):
         r, dt = oracle_reference(p, threads=cores, tol=1e-9)
         # time to k within 1e-6 of its own converged value
@@ -175,7 +186,7 @@ def run_reference(args, p):
                                        "iterate within 1e-6 of the converged k"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "k": kref}
-    del mp
+    line["cpu_baseline"]["cpu_model"] = cpu_model()
     return line
 
 

@@ -278,6 +278,15 @@ typedef struct {
   const double *psi0_cores; /* optional host TT initial guess (rank-1 cores), NULL = ones */
   int mv_kind;       /* product B = (S + F/k) Psi: 0 the AMEn product (the paper's choice),
                         1 the exact TT product (core-wise Kronecker) rounded at eps / rmax */
+  int local_form;    /* local systems of the linear solve M Psi' = B (M = H, or H - S with scheme 1):
+                        0 Galerkin projections of M (what AMEn does);
+                        1 least squares, the functional ||M Psi' - B||^2 of Eq. (linear_system_obj):
+                          projections of N = M^T M (built once per problem as the sum over
+                          octant row blocks of M_o^T M_o, rounded at eps_op) with right-hand side
+                          M^T B.  The symmetric part of the vertex diamond-difference H is
+                          indefinite, so a Galerkin projection of H onto rank-capped frames can
+                          be singular; N's projections are symmetric positive definite.
+                        Applies to keig_fixed_point (other entry points use 0). */
 } keig_opts;
 
 typedef struct {
@@ -292,7 +301,7 @@ typedef struct {
 
 /* Fill opts with defaults (eps 1e-7, rmax 64, tol_k 1e-9, tol_psi 1e-5,
  * max_iter 400, solve_sweeps 2, mv_sweeps 2, kick 4, scheme 0, FP64,
- * eps_op 1e-12, AMEn product). */
+ * eps_op 1e-12, AMEn product, Galerkin local systems). */
 int keig_default_opts(keig_opts *opts);
 
 /* The QTT fixed point of Eq. (TT_k_eff_fixed_points):

@@ -48,7 +48,7 @@ class KeigOpts(C.Structure):
         ("eps", C.c_double), ("rmax", C.c_int), ("tol_k", C.c_double), ("tol_psi", C.c_double),
         ("max_iter", C.c_int), ("solve_sweeps", C.c_int), ("mv_sweeps", C.c_int), ("kick", C.c_int),
         ("scheme", C.c_int), ("prec", C.c_int), ("eps_op", C.c_double), ("psi0_cores", D),
-        ("mv_kind", C.c_int),
+        ("mv_kind", C.c_int), ("local_form", C.c_int),
     ]
 
 

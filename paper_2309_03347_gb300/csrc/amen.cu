@@ -388,9 +388,10 @@ void orth_core_cols(Ctx *c, TT &z, int k, const double *blk) {
 }  // namespace
 
 void amen_solve(Ctx *c, TTOp &Aop, const TT &b, TT &x, double eps, int rmax, int nswp, int kick, uint64_t seed,
-                SolveStats *st, int prec) {
+                SolveStats *st, int prec, TTOp *rhs_op) {
   TT &A = Aop.t;
   Aop.prepare(c);
+  if (rhs_op) rhs_op->prepare(c);
   const bool use_tc = prec == TT_TF32_SPLIT;
   const bool mixed = prec == TT_FP32_REFINED || use_tc;
   if (mixed) Aop.prepare32(c);
@@ -399,6 +400,34 @@ void amen_solve(Ctx *c, TTOp &Aop, const TT &b, TT &x, double eps, int rmax, int
   TT_REQUIRE(b.d == d && x.d == d, "amen_solve: dimension mismatch");
   for (int k = 0; k < d; ++k)
     TT_REQUIRE(A.mo[k] == A.mi[k] && A.mi[k] == x.n[k] && b.n[k] == x.n[k], "amen_solve: mode mismatch");
+  if (rhs_op)
+    for (int k = 0; k < d; ++k)
+      TT_REQUIRE(rhs_op->t.d == d && rhs_op->t.mo[k] == x.n[k] && rhs_op->t.mi[k] == b.n[k],
+                 "amen_solve: rhs operator mode mismatch");
+  DBuf T1, T2, T3;
+  // Right-hand-side pieces through the frames y (x or z): plain b (interfaces
+  // y'b, (r_y, r_b)) or rhs_op b (interfaces y' rhs_op b, (r_y, R, r_b)).
+  auto rhs_local = [&](int k, const double *L, const double *R, int ry0, int ry1, double *out) {
+    if (!rhs_op)
+      vlocal(c, L, b.core[k].p(), R, ry0, b.r[k], b.n[k], b.r[k + 1], ry1, out, T3);
+    else
+      local_matvec(c, L, rhs_op->a_ajib[k].p(), R, b.core[k].p(), ry0, rhs_op->t.r[k], b.r[k], x.n[k], b.n[k],
+                   rhs_op->t.r[k + 1], ry1, b.r[k + 1], out, T1, T2);
+  };
+  auto rhs_left = [&](int k, const double *L, const double *y, int ry0, int ry1, DBuf &out) {
+    if (!rhs_op)
+      vleft_update(c, L, y, b.core[k].p(), ry0, b.r[k], x.n[k], ry1, b.r[k + 1], out, T3);
+    else
+      left_update(c, L, y, rhs_op->a_ajib[k].p(), b.core[k].p(), ry0, rhs_op->t.r[k], b.r[k], x.n[k], b.n[k],
+                  rhs_op->t.r[k + 1], ry1, b.r[k + 1], out, T1, T2);
+  };
+  auto rhs_right = [&](int k, const double *R, const double *y, int ry0, int ry1, DBuf &out) {
+    if (!rhs_op)
+      vright_update(c, R, y, b.core[k].p(), ry0, b.r[k], x.n[k], ry1, b.r[k + 1], out, T3);
+    else
+      right_update(c, R, y, rhs_op->a_jbai[k].p(), b.core[k].p(), ry0, rhs_op->t.r[k], b.r[k], x.n[k], b.n[k],
+                   rhs_op->t.r[k + 1], ry1, b.r[k + 1], out, T1, T2);
+  };
   const double loc_eps = eps / std::sqrt((double)d);
   TT z = tt_random(c, x.n, std::max(kick, 1), seed);
   orth_right(c, x, 0);
@@ -408,18 +437,15 @@ void amen_solve(Ctx *c, TTOp &Aop, const TT &b, TT &x, double eps, int rmax, int
   QX.init(c, d);
   PZ.init(c, d);
   QZ.init(c, d);
-  DBuf T1, T2, T3;
   auto right_all = [&]() {
     for (int k = d - 1; k >= 1; --k) {
       const int m = x.n[k], R1 = A.r[k], R2 = A.r[k + 1];
       right_update(c, PX.R[k + 1].p(), x.core[k].p(), Aop.a_jbai[k].p(), x.core[k].p(), x.r[k], R1, x.r[k], m, m,
                    R2, x.r[k + 1], x.r[k + 1], PX.R[k], T1, T2);
-      vright_update(c, QX.R[k + 1].p(), x.core[k].p(), b.core[k].p(), x.r[k], b.r[k], m, x.r[k + 1], b.r[k + 1],
-                    QX.R[k], T3);
+      rhs_right(k, QX.R[k + 1].p(), x.core[k].p(), x.r[k], x.r[k + 1], QX.R[k]);
       right_update(c, PZ.R[k + 1].p(), z.core[k].p(), Aop.a_jbai[k].p(), x.core[k].p(), z.r[k], R1, x.r[k], m, m,
                    R2, z.r[k + 1], x.r[k + 1], PZ.R[k], T1, T2);
-      vright_update(c, QZ.R[k + 1].p(), z.core[k].p(), b.core[k].p(), z.r[k], b.r[k], m, z.r[k + 1], b.r[k + 1],
-                    QZ.R[k], T3);
+      rhs_right(k, QZ.R[k + 1].p(), z.core[k].p(), z.r[k], z.r[k + 1], QZ.R[k]);
     }
   };
   right_all();
@@ -437,7 +463,7 @@ void amen_solve(Ctx *c, TTOp &Aop, const TT &b, TT &x, double eps, int rmax, int
       const int r0 = x.r[k], r1 = x.r[k + 1];
       const size_t N = (size_t)r0 * m * r1;
       rhs.ensure(c, N);
-      vlocal(c, QX.L[k].p(), b.core[k].p(), QX.R[k + 1].p(), r0, b.r[k], m, b.r[k + 1], r1, rhs.p(), T3);
+      rhs_local(k, QX.L[k].p(), QX.R[k + 1].p(), r0, r1, rhs.p());
       sol.ensure(c, N);
       copy(c, sol.p(), x.core[k].p(), N);
       auto mv = [&](const double *in, double *out) {
@@ -512,14 +538,14 @@ void amen_solve(Ctx *c, TTOp &Aop, const TT &b, TT &x, double eps, int rmax, int
       PhaseTimer pt_res(c, "amen.residual");
       // crz = x'b z - x'Ax z . solt     (r0, m, rz1)
       crz.ensure(c, (size_t)r0 * m * rz1);
-      vlocal(c, QX.L[k].p(), b.core[k].p(), QZ.R[k + 1].p(), r0, b.r[k], m, b.r[k + 1], rz1, crz.p(), T3);
+      rhs_local(k, QX.L[k].p(), QZ.R[k + 1].p(), r0, rz1, crz.p());
       tmp.ensure(c, (size_t)r0 * m * rz1);
       local_matvec(c, PX.L[k].p(), Aop.a_ajib[k].p(), PZ.R[k + 1].p(), solt.p(), r0, R1, r0, m, m, R2, rz1, r1,
                    tmp.p(), T1, T2);
       axpby(c, (size_t)r0 * m * rz1, -1.0, tmp.p(), 1.0, crz.p());
       // czz = z'b z - z'Ax z . solt     (rz0, m, rz1)
       czz.ensure(c, (size_t)rz0 * m * rz1);
-      vlocal(c, QZ.L[k].p(), b.core[k].p(), QZ.R[k + 1].p(), rz0, b.r[k], m, b.r[k + 1], rz1, czz.p(), T3);
+      rhs_local(k, QZ.L[k].p(), QZ.R[k + 1].p(), rz0, rz1, czz.p());
       tmp.ensure(c, (size_t)rz0 * m * rz1);
       local_matvec(c, PZ.L[k].p(), Aop.a_ajib[k].p(), PZ.R[k + 1].p(), solt.p(), rz0, R1, r0, m, m, R2, rz1, r1,
                    tmp.p(), T1, T2);
@@ -533,10 +559,10 @@ void amen_solve(Ctx *c, TTOp &Aop, const TT &b, TT &x, double eps, int rmax, int
       PhaseTimer pt_if(c, "amen.iface");
       left_update(c, PX.L[k].p(), x.core[k].p(), Aop.a_ajib[k].p(), x.core[k].p(), r0, R1, r0, m, m, R2, nr1, nr1,
                   PX.L[k + 1], T1, T2);
-      vleft_update(c, QX.L[k].p(), x.core[k].p(), b.core[k].p(), r0, b.r[k], m, nr1, b.r[k + 1], QX.L[k + 1], T3);
+      rhs_left(k, QX.L[k].p(), x.core[k].p(), r0, nr1, QX.L[k + 1]);
       left_update(c, PZ.L[k].p(), z.core[k].p(), Aop.a_ajib[k].p(), x.core[k].p(), rz0, R1, r0, m, m, R2, rz1, nr1,
                   PZ.L[k + 1], T1, T2);
-      vleft_update(c, QZ.L[k].p(), z.core[k].p(), b.core[k].p(), rz0, b.r[k], m, rz1, b.r[k + 1], QZ.L[k + 1], T3);
+      rhs_left(k, QZ.L[k].p(), z.core[k].p(), rz0, rz1, QZ.L[k + 1]);
     }
     if (maxdx < eps) {
       ++swp;

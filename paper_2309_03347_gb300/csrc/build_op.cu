@@ -248,7 +248,8 @@ OpFactors make_factors(Ctx *c, const tt_problem *p) {
   return F;
 }
 
-TT assemble_operator(Ctx *c, const tt_problem *p, const OpFactors &F, int kind, int only_mat, double eps_op) {
+TT assemble_operator(Ctx *c, const tt_problem *p, const OpFactors &F, int kind, int only_mat, double eps_op,
+                     int only_oct) {
   const int l = p->l, G = p->G, nd = p->n_dir, nm = p->n_mat;
   // derivative kinds omit the group core (the operator is linear in the group matrix)
   const bool group_core = !(kind == KIND_COLLISION || kind == KIND_SOURCE);
@@ -268,6 +269,7 @@ TT assemble_operator(Ctx *c, const tt_problem *p, const OpFactors &F, int kind, 
   for (int a = 0; a < nd; ++a)
     for (int b = 0; b < nd; ++b) dirm[(size_t)a * nd + b] = p->w[b];
   for (int o = 0; o < 8; ++o) {
+    if (only_oct >= 0 && o != only_oct) continue;  // the rows of one octant only
     const int px = (o & 1) ? 1 : 0, py = (o & 2) ? 1 : 0, pz = (o & 4) ? 1 : 0;
     std::vector<double> E(64, 0.0), Intg(64, 0.0);
     E[o * 8 + o] = 1.0;

@@ -514,6 +514,7 @@ int keig_default_opts(keig_opts *o) {
   o->eps_op = 1e-12;
   o->psi0_cores = nullptr;
   o->mv_kind = 0;
+  o->local_form = 0;
   return TT_OK;
 }
 
@@ -530,6 +531,7 @@ void check_opts(const keig_opts *opts) {
   TT_REQUIRE(opts->eps > 0 && opts->eps < 1 && opts->max_iter >= 1, "keig: bad eps/max_iter");
   TT_REQUIRE(opts->scheme == 0 || opts->scheme == 1, "keig: scheme must be 0 or 1");
   TT_REQUIRE(opts->mv_kind == 0 || opts->mv_kind == 1, "keig: mv_kind must be 0 or 1");
+  TT_REQUIRE(opts->local_form == 0 || opts->local_form == 1, "keig: local_form must be 0 or 1");
 }
 
 // The operators of one problem, forward or transposed (adjoint).
@@ -537,7 +539,40 @@ struct KeigOps {
   tt::TTOp LHS, RHS;  // scheme 0: H and S (+) F; scheme 1: H - S and F
   tt::TT f;           // sum(F Psi) = <f, Psi>
   int rS = 0;         // columns of the first RHS core that belong to S (scheme 0)
+  bool ls = false;    // least-squares local systems: solve N Psi' = M^T B
+  tt::TTOp N, MT;     // N = M^T M and M^T for the system matrix M (= LHS)
 };
+
+// N = M^T M for M = sum_b M_b whose row blocks M_b have disjoint rows
+// (so M^T M = sum_b M_b^T M_b): each product is rounded before it is added.
+tt::TT normal_operator(tt::Ctx *c, const std::vector<tt::TT> &blocks, double eps_op) {
+  tt::TT N;
+  for (size_t b = 0; b < blocks.size(); ++b) {
+    for (int k = 1; k < blocks[b].d; ++k)
+      TT_REQUIRE((long long)blocks[b].r[k] * blocks[b].r[k] <= 512,
+                 "least-squares local systems: an operator block's rank is above 22");
+    tt::TT P = tt::op_matmul_tn(c, blocks[b], blocks[b]);
+    tt::round(c, P, eps_op, 0);
+    if (b == 0) {
+      N = std::move(P);
+    } else {
+      N = tt::add(c, 1.0, N, 1.0, P);
+      tt::round(c, N, eps_op, 0);
+    }
+  }
+  return N;
+}
+
+// The least-squares form of the linear solve (Eq. (linear_system_obj):
+// minimise ||M Psi' - B||): its local systems are the projections of
+// N = M^T M with right-hand side M^T B.  blocks: row blocks of M (empty: M
+// itself as one block).
+void make_ls(tt::Ctx *c, KeigOps &o, std::vector<tt::TT> blocks, const keig_opts *opts) {
+  if (blocks.empty()) blocks.push_back(tt::tt_clone(c, o.LHS.t));
+  o.N.t = normal_operator(c, blocks, opts->eps_op);
+  o.MT.t = tt::transpose_op(c, o.LHS.t);
+  o.ls = true;
+}
 
 KeigOps make_ops(tt::Ctx *c, tt::TT H, tt::TT S, tt::TT F, const keig_opts *opts) {
   KeigOps o;
@@ -605,8 +640,12 @@ bool run_fixed_point(tt::Ctx *c, KeigOps &ops, const keig_opts *opts, keig_resul
     tt::TT psi_new = tt::tt_clone(c, psi);
     {
       tt::PhaseTimer pt(c, "keig.solve");
-      tt::amen_solve(c, ops.LHS, B, psi_new, opts->eps, opts->rmax, opts->solve_sweeps, opts->kick,
-                     seed + 5000 + it, &sst, (int)opts->prec);
+      if (ops.ls)
+        tt::amen_solve(c, ops.N, B, psi_new, opts->eps, opts->rmax, opts->solve_sweeps, opts->kick,
+                       seed + 5000 + it, &sst, (int)opts->prec, &ops.MT);
+      else
+        tt::amen_solve(c, ops.LHS, B, psi_new, opts->eps, opts->rmax, opts->solve_sweeps, opts->kick,
+                       seed + 5000 + it, &sst, (int)opts->prec);
     }
     if (c->phase_timing)
       fprintf(stderr, "keig it %d k %.12f mv_sweeps %d mv_dx %.2e solve_sweeps %d solve_dx %.2e gmres %lld ranks B %d psi %d\n",
@@ -701,14 +740,29 @@ int keig_fixed_point(tt_ctx *ctx, const tt_problem *prob, const keig_opts *opts,
     memset(out, 0, sizeof(*out));
     // operators (Sec. 3.2-3.3)
     tt::TT H, S, F;
+    std::vector<tt::TT> blocks;  // octant row blocks of the system matrix (least-squares form)
     {
       tt::PhaseTimer pt(c, "keig.build_ops");
       tt::OpFactors fac = tt::make_factors(c, prob);
       H = tt::assemble_operator(c, prob, fac, TT_OP_H, -1, opts->eps_op);
       S = tt::assemble_operator(c, prob, fac, TT_OP_S, -1, opts->eps_op);
       F = tt::assemble_operator(c, prob, fac, TT_OP_F, -1, opts->eps_op);
+      if (opts->local_form == 1)
+        for (int o = 0; o < 8; ++o) {
+          tt::TT Ho = tt::assemble_operator(c, prob, fac, TT_OP_H, -1, opts->eps_op, o);
+          if (opts->scheme == 1) {
+            tt::TT So = tt::assemble_operator(c, prob, fac, TT_OP_S, -1, opts->eps_op, o);
+            Ho = tt::add(c, 1.0, Ho, -1.0, So);
+            tt::round(c, Ho, opts->eps_op, 0);
+          }
+          blocks.push_back(std::move(Ho));
+        }
     }
     KeigOps ops = make_ops(c, std::move(H), std::move(S), std::move(F), opts);
+    if (opts->local_form == 1) {
+      tt::PhaseTimer pt(c, "keig.build_normal");
+      make_ls(c, ops, std::move(blocks), opts);
+    }
     tt::TT psi;
     conv = run_fixed_point(c, ops, opts, out, psi, t0, 0);
     if (phi_out) {

@@ -83,6 +83,7 @@ void scale(Ctx *c, TT &x, double a);
 TT add(Ctx *c, double a, const TT &x, double b, const TT &y);
 TT matvec_exact(Ctx *c, const TT &A, const TT &x);
 TT transpose_op(Ctx *c, const TT &A);
+TT op_matmul_tn(Ctx *c, const TT &A, const TT &B);  // A^T B, ranks multiply
 void to_dense(Ctx *c, const TT &x, double *dst, size_t len);
 TT tt_svd_dense(Ctx *c, const double *a, const std::vector<int> &modes, double eps, int rmax);
 
@@ -92,8 +93,11 @@ struct SolveStats {
   double max_dx = 0.0;
   long long gmres_iters = 0;
 };
+// A x = b by AMEn with Galerkin local systems; with rhs_op the right-hand side
+// is rhs_op b (projected through operator interfaces), which with A = M^T M and
+// rhs_op = M^T gives the least-squares local systems of min ||M x - b||
 void amen_solve(Ctx *c, TTOp &A, const TT &b, TT &x, double eps, int rmax, int nswp, int kick,
-                uint64_t seed, SolveStats *st, int prec = TT_FP64);
+                uint64_t seed, SolveStats *st, int prec = TT_FP64, TTOp *rhs_op = nullptr);
 void amen_mv(Ctx *c, TTOp &A, const TT &x, TT &y, double eps, int rmax, int nswp, int kick,
              uint64_t seed, SolveStats *st);
 // interface updates (amen.cu); operator cores in the permuted layouts of TTOp
@@ -115,7 +119,10 @@ struct OpFactors {
 // structure without their group core (derivatives w.r.t. the group matrices)
 enum { KIND_COLLISION = 10, KIND_SOURCE = 11 };
 OpFactors make_factors(Ctx *c, const tt_problem *p);
-TT assemble_operator(Ctx *c, const tt_problem *p, const OpFactors &F, int kind, int only_mat, double eps_op);
+// only_oct >= 0: the rows of that octant only (every term of H, S and F has
+// its rows in one octant, so the operator is the sum of its octant row blocks)
+TT assemble_operator(Ctx *c, const tt_problem *p, const OpFactors &F, int kind, int only_mat, double eps_op,
+                     int only_oct = -1);
 TT build_operator(Ctx *c, const tt_problem *p, int kind, double eps_op);
 // H, S or F of a 1-D slab over the modes [G][2][n_dir][x bits]
 TT assemble_slab_operator(Ctx *c, const tt_slab *s, int kind, double eps_op);

@@ -350,6 +350,48 @@ TT transpose_op(Ctx *c, const TT &A) {
   return B;
 }
 
+// A^T B of two TT matrices, core by core (ranks multiply):
+//   C_k[(a, b), i, j, (a', b')] = sum_l A_k[a, l, i, a'] B_k[b, l, j, b'],
+// one GEMM over the shared index l per core between the permuted cores
+// A' (l; a i a') and B' (l; b j b'), then a permute of the product
+// (a i a', b j b') into (a b, i, j, a' b').
+TT op_matmul_tn(Ctx *c, const TT &A, const TT &B) {
+  TT_REQUIRE(A.d == B.d && A.is_matrix() && B.is_matrix(), "op_matmul_tn: operands must be TT matrices of one d");
+  const int d = A.d;
+  TT C;
+  C.d = d;
+  C.r.resize(d + 1);
+  C.mo.resize(d);
+  C.mi.resize(d);
+  C.n.resize(d);
+  C.core.resize(d);
+  for (int k = 0; k <= d; ++k) C.r[k] = A.r[k] * B.r[k];
+  DBuf Ap, Bp, P;
+  for (int k = 0; k < d; ++k) {
+    TT_REQUIRE(A.mo[k] == B.mo[k], "op_matmul_tn: the shared (row) modes differ");
+    const int ra = A.r[k], rb = B.r[k], ra1 = A.r[k + 1], rb1 = B.r[k + 1];
+    const int L = A.mo[k], mi = A.mi[k], mj = B.mi[k];
+    C.mo[k] = mi;
+    C.mi[k] = mj;
+    C.n[k] = mi * mj;
+    const int shA[4] = {ra, L, mi, ra1}, shB[4] = {rb, L, mj, rb1};
+    const int pl[4] = {1, 0, 2, 3};
+    Ap.ensure(c, A.csize(k));
+    Bp.ensure(c, B.csize(k));
+    permute(c, A.core[k].p(), Ap.p(), 4, shA, pl);  // (l, a, i, a')
+    permute(c, B.core[k].p(), Bp.p(), 4, shB, pl);  // (l, b, j, b')
+    const int M = ra * mi * ra1, N = rb * mj * rb1;
+    P.ensure(c, (size_t)M * N);
+    gemm(c, true, false, M, N, L, 1.0, Ap.p(), M, 0, Bp.p(), N, 0, 0.0, P.p(), N, 0);
+    // (a, i, a', b, j, b') -> (a, b, i, j, a', b')
+    const int shP[6] = {ra, mi, ra1, rb, mj, rb1};
+    const int pp[6] = {0, 3, 1, 4, 2, 5};
+    C.core[k].alloc(c, (size_t)M * N);
+    permute(c, P.p(), C.core[k].p(), 6, shP, pp);
+  }
+  return C;
+}
+
 void TTOp::prepare(Ctx *c) {
   if (prepared) return;
   a_ajib.resize(t.d);
