@@ -1,18 +1,27 @@
 """Benchmark: time to a k-eigenvalue solution within 1e-6 of the FP64 oracle,
-with the contraction kernel's FP64 throughput against its roofline.
+with the dominant contraction kernel's throughput against its roofline.
 
-One step = one call of keig_fixed_point on the synthetic workload (operator
-construction, QTT fixed point to the solver's own stop), inputs resident on
-the device side of the library when the timed region starts (the problem
-tables are a few KB and are copied inside the call).  `value` is seconds per
-solve measured with CUDA events on the library stream; `e2e` is the same call
-timed on the host with the scalar flux copied back to host memory.
+One step = one call of keig_fixed_point (operator construction, then the
+QTT fixed point of Eq. (TT_k_eff_fixed_points)) run for the number of outer
+iterations after which every iterate stays within 1e-6 of the oracle's k
+(found in the first warm-up solve).  `value` is seconds per such solve,
+measured with CUDA events on the library stream, problem tables resident on
+the host side of the library (a few KB, copied inside the call); `e2e` is the
+same call timed on the host with the tables in pinned host memory and the
+scalar flux copied back to pinned host memory.
+
+The default workload is the paper's 3-D benchmark geometry (Sec. 4.2): a bare
+homogeneous cube of 10 cm with vacuum faces at 128 grid points per axis, with
+seeded synthetic 2-group cross sections and an S4 level-symmetric set in
+place of the unavailable 256-group data and the S8 square set.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                       [--workload NAME] [--prec mixed|tf32|bf16|fp64]
 """
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import statistics
@@ -30,50 +39,77 @@ import keig_inputs as ki  # noqa: E402
 
 METRIC = "time to k within 1e-6 of FP64 oracle; TT contraction TFLOP/s and % of peak"
 UNIT = "s"
-FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 rate from the profiling recipe's table (nominal)
+GOLDEN = os.path.join(ROOT, "tests", "golden", "oracle_reference.txt")
 
-
-def workload():
-    p = ki.config(1)
-    return p
-
-
-def opts_for(K, p, prec="mixed"):
-    o = K.keig_default_opts()
-    o.eps, o.rmax = p.eps, p.rmax
-    o.tol_k, o.tol_psi, o.max_iter = 1e-9, 1e-5, 20
-    o.solve_sweeps, o.mv_sweeps, o.kick = 2, 2, 4
-    o.scheme = 0
-    o.prec = {"mixed": K.TT_FP32_REFINED, "tf32": K.TT_TF32_SPLIT, "fp64": K.TT_FP64}[prec]
-    return o
-
+# name -> (problem, rank cap, eps, local form (0 Galerkin, 1 least squares), note)
+WORKLOADS = {
+    "cube128_g2_s4_10cm": (lambda: ki.bare_cube(7), 64, 1e-8, 1,
+                           "bare homogeneous 10 cm cube, 128^3 grid points (the paper's Sec. 4.2 geometry at its "
+                           "smallest grid), 2 groups, S4 level-symmetric (24 directions), vacuum"),
+    "cube64_g2_s4_10cm": (lambda: ki.bare_cube(6), 64, 1e-8, 1,
+                          "bare homogeneous 10 cm cube, 64^3 grid points, 2 groups, S4, vacuum"),
+    "box32_g4_s8": (lambda: ki.config(1), 64, 1e-7, 0,
+                    "fissile box in a c = 0.9 reflector, 32^3, 4 groups, S8 (its rank cap 64 limits k to about "
+                    "5e-5 of the oracle: this workload cannot reach 1e-6)"),
+}
+DEFAULT_WORKLOAD = "cube128_g2_s4_10cm"
 
 PRECISION_TEXT = {
     "mixed": "FP32 Krylov contractions (SIMT) in FP64 iterative refinement; FP64 products, rounding, k",
     "tf32": ("FP32 Krylov contractions on tcgen05 tensor cores (TF32 three-term split, FP32 accumulation) "
              "in FP64 iterative refinement; FP64 products, rounding, k"),
+    "bf16": ("FP32 Krylov contractions on tcgen05 tensor cores (BF16 three-term split, FP32 accumulation) "
+             "in FP64 iterative refinement; FP64 products, rounding, k"),
     "fp64": "FP64 throughout",
 }
-DTYPE_TEXT = {"mixed": "f64+f32", "tf32": "f64+tf32x3", "fp64": "f64"}
+DTYPE_TEXT = {"mixed": "f64+f32", "tf32": "f64+tf32x3", "bf16": "f64+bf16x3", "fp64": "f64"}
 
 
-def tf32_tensor_peak_tflops():
-    """Dense TF32 tensor rate: the measured sustained bf16 cuBLAS rate of
-    MEASURED_PEAKS.json times the nominal tf32/bf16 ratio (1.1 / 2.25)."""
+def golden_reference(name):
+    """(k, oracle iterations to 1e-6) stored by tests/golden/make_oracle_reference.py, or None."""
+    if os.path.exists(GOLDEN):
+        for line in open(GOLDEN):
+            if line.strip() and not line.startswith("#"):
+                f = line.split()
+                if f[0] == name:
+                    return float(f[1]), int(f[3])
+    return None
+
+
+def cpu_model():
+    """The host CPU's model name (from /proc/cpuinfo; 'unknown' if absent)."""
     try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            bf16 = float(json.load(f)["bf16_tflops_sustained"])
-        src = "measured sustained bf16 x 1.1/2.25 (nominal tf32/bf16)"
-    except (OSError, KeyError, ValueError):
-        bf16 = 1700.0
-        src = "fallback sustained bf16 x 1.1/2.25 (nominal tf32/bf16)"
-    return bf16 * 1.1 / 2.25, src
+        for line in open("/proc/cpuinfo"):
+            key = line.split(":")[0].strip().lower()
+            if key in ("model name", "cpu part", "hardware"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine() or "unknown"
 
 
-# FP32 SIMT peak of the part from its unit counts and clock: 152 SMs x 128
-# FP32 lanes x 2 flops (FMA) x the maximum SM clock.
-def fp32_simt_peak_tflops(sm_mhz=2070.0, sms=152):
-    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+def oracle_ref(p, name, threads=0):
+    """k of the oracle (stored for the large workloads, else computed here)
+    and the oracle iterations after which its k stays within 1e-6."""
+    g = golden_reference(name)
+    if g is not None:
+        return g[0], g[1], "stored (tests/golden/oracle_reference.txt)"
+    from oracle import transport as T
+    r = T.OracleProblem(p, threads=threads).keig(tol_k=1e-13, max_iter=100000, history=True)
+    ks = r["k_hist"]
+    n_ok = next(i for i in range(len(ks)) if np.all(np.abs(ks[i:] - r["k"]) < 1e-6 * r["k"])) + 1
+    return r["k"], n_ok, "computed by the oracle in this run"
+
+
+def oracle_sample(p, n_iter, threads):
+    """Seconds per oracle power iteration on `threads` host cores, timed over
+    n_iter iterations of the same workload (a bounded sample)."""
+    from oracle import transport as T
+    op = T.OracleProblem(p, threads=threads)
+    t0 = time.time()
+    op.keig(tol_k=0.0, max_iter=n_iter)
+    return (time.time() - t0) / n_iter
 
 
 class Clocks:
@@ -133,61 +169,67 @@ def max_over_ranks(value, dist=None, device="cpu"):
     return float(t.item())
 
 
-def oracle_reference(p, threads=0, tol=1e-10):
-    from oracle import transport as T
-    t0 = time.time()
-    r = T.OracleProblem(p, threads=threads).keig(tol_k=tol, max_iter=20000, history=True)
-    return r, time.time() - t0
-
-
-def first_within(k_hist, t_hist, k_ref, tol=1e-6):
-    """Time (ms) of the first iterate from which k stays within tol of k_ref."""
-    err = np.abs(np.asarray(k_hist) - k_ref) / abs(k_ref)
-    ok = err < tol
-    for i in range(len(ok)):
-        if ok[i:].all():
-            return float(t_hist[i]), i + 1
-    return None, None
-
-
-def cpu_model():
-    """The host CPU's model name (from /proc/cpuinfo; 'unknown' if absent)."""
-    try:
-        for line in open("/proc/cpuinfo"):
-            key = line.split(":")[0].strip().lower()
-            if key in ("model name", "cpu part", "hardware"):
-                return line.split(":", 1)[1].strip()
-    except OSError:
-        pass
-    import platform
-    return platform.processor() or platform.machine() or "unknown"
-
-
-def run_reference(args, p):
-    """The oracle (plain FP64 CPU power iteration) on the same workload; the
-    CPU program keeps no state between runs, so it needs no warm-up."""
+def run_reference(args, name):
+    """The oracle (plain FP64 CPU power iteration, the paper's fixed point on
+    the full grid) on the same workload: time per iteration from a bounded
+    sample of iterations, times the iterations the oracle needs to stay
+    within 1e-6 of its converged k."""
+    p = WORKLOADS[name][0]()
     cores = os.cpu_count() or 1
-    times, kref = [], None
-    for _ in range(args.steps):
-        r, dt = oracle_reference(p, threads=cores, tol=1e-9)
-        # time to k within 1e-6 of its own converged value
-        ks = r["k_hist"]
-        kref = r["k"]
-        n_ok = next(i for i in range(len(ks)) if np.all(np.abs(ks[i:] - kref) / kref < 1e-6)) + 1
-        times.append(dt * n_ok / max(r["iters"], 1))
+    kref, n_ok, src = oracle_ref(p, name, threads=cores)
+    sample_it = max(2, min(10, int(20.0 / max(1e-9, 4e-9 * p.G * p.L * p.n ** 3))))
+    times = [oracle_sample(p, sample_it, cores) * n_ok for _ in range(max(1, args.steps))]
     v = float(np.median(times))
-    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+    sample = (f"{sample_it} oracle iterations per step on {cores} cores, scaled to the {n_ok} iterations after "
+              f"which its k stays within 1e-6 of its converged value (k {src})")
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": p.name, "grid": f"{p.n}^3", "groups": p.G, "directions": p.L,
+            "config": {"workload": name, "grid": f"{p.n}^3", "groups": p.G, "directions": p.L,
                        "side_cm": p.side[0]},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": "full power iteration to |dk| < 1e-9; time scaled to the first "
-                                       "iterate within 1e-6 of the converged k"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                             "cpu_model": cpu_model()},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "k": kref}
-    line["cpu_baseline"]["cpu_model"] = cpu_model()
-    return line
+
+
+def measured_peaks(K):
+    """Live roofline denominators (TFLOP/s): the library's FP64 and FP32 FMA
+    streams and the cuBLAS TF32 and BF16 GEMM rates (torch.matmul)."""
+    from paper_2309_03347_gb300.peaks import measure_peaks
+    return measure_peaks(gemms=True)
+
+
+def make_opts(K, name, prec, max_iter):
+    _, cap, eps, lf, _ = WORKLOADS[name]
+    o = K.keig_default_opts()
+    o.eps, o.rmax = eps, cap
+    o.tol_k, o.tol_psi, o.max_iter = 1e-10, 1e-7, max_iter
+    o.solve_sweeps, o.mv_sweeps, o.kick = 2, 2, 4
+    o.scheme = 0
+    o.local_form = lf
+    o.prec = {"mixed": K.TT_FP32_REFINED, "tf32": K.TT_TF32_SPLIT, "bf16": K.TT_BF16_SPLIT,
+              "fp64": K.TT_FP64}[prec]
+    return o
+
+
+def first_within(k_hist, k_ref, tol=1e-6):
+    """1-based index of the first iterate from which every later k stays
+    within tol (relative) of k_ref, or None."""
+    err = np.abs(np.asarray(k_hist) - k_ref) / abs(k_ref)
+    for i in range(len(err)):
+        if np.all(err[i:] < tol):
+            return i + 1
+    return None
+
+
+def roof(name, n, gms, gfl, peak, source, ms_step, bound="alu"):
+    """Roofline entry of one kernel from its per-launch CUDA-event times."""
+    avg = gms / max(n, 1)
+    ach = (gfl / max(n, 1)) / (avg * 1e-3) / 1e12 if n and avg > 0 else 0.0
+    return {"bound": bound, "kernel": name, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+            "frac": ach / peak if peak else None, "traffic": None, "peak_source": source, "launches": n,
+            "avg_launch_us": avg * 1e3, "ms_in_step": gms, "share_of_step": gms / ms_step if ms_step else None}
 
 
 def main():
@@ -196,19 +238,21 @@ def main():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--prec", default="mixed", choices=["mixed", "tf32", "bf16", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--max-iter", type=int, default=None,
-                    help="cap the outer iterations (short runs for profiler captures)")
-    ap.add_argument("--prec", default="mixed", choices=["mixed", "tf32", "fp64"])
+                    help="run every solve for this many outer iterations (short runs for profiler captures)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
-    p = workload()
+    name = args.workload
+    p = WORKLOADS[name][0]()
 
     if args.impl == "reference":
         if rank == 0:
-            print(json.dumps(run_reference(args, p)))
+            print(json.dumps(run_reference(args, name)))
         return
 
     import torch
@@ -223,24 +267,33 @@ def main():
     g.build()
     import paper_2309_03347_gb300 as K
 
+    peaks = measured_peaks(K)
+    kref, n_ok_oracle, kref_src = oracle_ref(p, name, threads=os.cpu_count() or 1)
     ctx = K.tt_ctx_create()
-    opts = opts_for(K, p, args.prec)
-    if args.max_iter:
-        opts.max_iter = args.max_iter
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
 
-    def step(want_phi=False):
-        return K.keig_fixed_point(ctx, p, opts, want_phi=want_phi, allow_noconv=True)
+    def step(o, phi_out=None, prob=p):
+        return K.keig_fixed_point(ctx, prob, o, allow_noconv=True, phi_out=phi_out)
 
-    for _ in range(args.warmup):
+    # ---- warm-up: the first solve runs to the solver's own stop and fixes the
+    # number of outer iterations after which k stays within 1e-6 of the oracle
+    full = make_opts(K, name, args.prec, 400)
+    flush.fill_(1.0)
+    r0 = step(full)
+    n_ok = first_within(r0["k_hist"], kref)
+    if args.max_iter:
+        n_it = args.max_iter
+    else:
+        n_it = n_ok if n_ok is not None else r0["iters"]
+    opts = make_opts(K, name, args.prec, n_it)
+    for _ in range(max(0, args.warmup - 1)):
         flush.fill_(1.0)
-        step()
+        step(opts)
     torch.cuda.synchronize()
 
     # ---- device-timed steps
-    ev = []
-    results = []
+    ev, results = [], []
     ctx.reset_counters()
     if dist:
         dist.barrier()
@@ -251,7 +304,7 @@ def main():
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            results.append(step())
+            results.append(step(opts))
             b.record(stream)
             ev.append((a, b))
         torch.cuda.synchronize()
@@ -260,9 +313,11 @@ def main():
         dist.barrier()
     ms = [a.elapsed_time(b) for a, b in ev]
     ms_step = max_over_ranks(float(np.median(ms)), dist, "cuda")
+    errs = [abs(r["k"] - kref) / kref for r in results]
 
-    # ---- end to end: host wall time including the scalar-flux readback
-    # inputs (the problem tables) and the scalar-flux result in pinned host memory
+    # ---- end to end: host wall time of the same call through the public API,
+    # problem tables in pinned host memory (copied to the device inside the
+    # call) and the scalar flux copied back into a pinned host buffer
     pins = []  # keep the pinned tensors alive for the arrays that view them
 
     def pinned(a):
@@ -272,23 +327,23 @@ def main():
         out = t.numpy()
         out[...] = a
         return out
-    import dataclasses
     p_pin = dataclasses.replace(p, sig_t=pinned(p.sig_t), sig_s=pinned(p.sig_s), nu_sig_f=pinned(p.nu_sig_f),
                                 chi=pinned(p.chi), mat=pinned(p.mat))
     phi_pin = pinned(np.zeros((p.G, p.n, p.n, p.n)))
     e2e = []
-    for _ in range(max(1, args.steps)):
+    for _ in range(max(1, min(args.steps, 3))):
         flush.fill_(1.0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        r = K.keig_fixed_point(ctx, p_pin, opts, allow_noconv=True, phi_out=phi_pin)
+        step(opts, phi_out=phi_pin, prob=p_pin)
         e2e.append(time.perf_counter() - t0)
     phi_bytes = phi_pin.nbytes
     in_bytes = sum(x.nbytes for x in (p.sig_t, p.sig_s, p.nu_sig_f, p.chi, p.mat)) + 4 * p.quad.amu.nbytes
 
-    # ---- one instrumented step: per-launch device time of the contraction GEMM
+    # ---- one instrumented step: per-launch device time of the contraction kernels
     ctx.set_profiling(True)
-    step()
+    flush.fill_(1.0)
+    step(opts)
     n_gemm, gemm_ms, gemm_flops = ctx.gemm_stats()
     n32, gemm32_ms, gemm32_flops = ctx.gemm32_stats()
     ntc, gemmtc_ms, gemmtc_flops = ctx.gemmtc_stats()
@@ -298,58 +353,59 @@ def main():
     if rank != 0:
         return
     res = results[-1]
+    _, cap, eps, lf, note = WORKLOADS[name]
     line = {
         "metric": METRIC, "value": ms_step / 1e3, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": DTYPE_TEXT[args.prec], "data": "synthetic",
-        "config": {"workload": p.name, "grid": f"{p.n}^3", "groups": p.G, "directions": p.L,
-                   "side_cm": p.side[0], "rank_cap": p.rmax, "eps": p.eps, "scheme": "paper",
-                   "precision": PRECISION_TEXT[args.prec],
+        "config": {"workload": name, "description": note, "grid": f"{p.n}^3", "groups": p.G, "directions": p.L,
+                   "side_cm": p.side[0], "rank_cap": cap, "eps": eps, "scheme": "paper",
+                   "local_systems": "least squares (Eq. (linear_system_obj))" if lf else "Galerkin",
+                   "outer_iterations": n_it, "precision": PRECISION_TEXT[args.prec],
                    "l2": "flushed between steps (256 MB write)",
                    "parallelism": "replicas" if world > 1 else "single"},
-        "k": res["k"], "iters": res["iters"], "max_rank": res["max_rank"], "converged": res["code"] == 0,
+        "k": res["k"], "k_oracle": kref, "k_oracle_source": kref_src,
+        "k_rel_err": float(np.max(errs)), "within_1e-6": bool(n_ok is not None and max(errs) < 1e-6),
+        "time_to_1e-6_ms": ms_step if (n_ok is not None and not args.max_iter) else None,
+        "first_solve": {"iters": r0["iters"], "k_rel_err": abs(r0["k"] - kref) / kref, "wall_ms": r0["wall_ms"],
+                        "first_within_1e-6": n_ok,
+                        "t_at_first_within_ms": float(r0["t_hist"][n_ok - 1]) if n_ok else None},
+        "max_rank": res["max_rank"],
         "gpu_launches": int(launches // max(args.steps, 1)),
         "e2e": {"value": float(np.median(e2e)), "unit": UNIT, "h2d_bytes_per_step": int(in_bytes),
                 "d2h_bytes_per_step": int(phi_bytes)},
+        "peaks_tflops": {k: v for k, v in peaks.items() if isinstance(v, float)},
     }
-    def roof(name, n, gms, gfl, peak, source, bound="alu"):
-        avg = gms / max(n, 1)
-        ach = (gfl / max(n, 1)) / (avg * 1e-3) / 1e12 if n else 0.0
-        return {"bound": bound, "kernel": name, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": None, "peak_source": source, "launches": n,
-                "avg_launch_us": avg * 1e3, "ms_in_step": gms, "share_of_step": gms / ms_step if ms_step else None}
-
-    sm_max = clk.summary().get("sm_max_mhz") or 2070.0
-    r64 = roof("dgemm_kernel (FP64 contraction GEMM)", n_gemm, gemm_ms, gemm_flops, FP64_NOMINAL_TFLOPS,
-               "nominal FP64 rate of the recipe table (MEASURED_PEAKS.json has no FP64 entry)")
-    r32 = roof("sgemm_kernel (FP32 contraction GEMM of the mixed-precision solves)", n32, gemm32_ms, gemm32_flops,
-               fp32_simt_peak_tflops(sm_max),
-               "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock (MEASURED_PEAKS.json has no FP32 entry)")
-    tf32_peak, tf32_src = tf32_tensor_peak_tflops()
-    rtc = roof("tc_gemm_kernel (tcgen05 TF32 three-term contraction GEMM; 3 MMA passes per product, "
-               "so frac <= 1/3)", ntc, gemmtc_ms, gemmtc_flops, tf32_peak, tf32_src, bound="tensor")
+    src_fma = "measured live: the library's FMA-stream kernel (tt_measure_fma_peak)"
+    tc_peak = peaks["bf16_gemm"] if args.prec == "bf16" else peaks["tf32_gemm"]
+    r64 = roof("dgemm_kernel (FP64 contraction GEMM)", n_gemm, gemm_ms, gemm_flops, peaks["fp64_fma"],
+               src_fma + ", FP64", ms_step)
+    r32 = roof("sgemm_kernel (FP32 SIMT contraction GEMM)", n32, gemm32_ms, gemm32_flops, peaks["fp32_fma"],
+               src_fma + ", FP32", ms_step)
+    rtc = roof("tc_gemm_kernel (tcgen05 three-term split GEMM; 3 MMA passes per product, so frac <= 1/3)",
+               ntc, gemmtc_ms, gemmtc_flops, tc_peak,
+               "measured live: cuBLAS " + ("BF16" if args.prec == "bf16" else "TF32") + " GEMM 8192^3",
+               ms_step, bound="tensor")
     rpg = roof("pgmres_kernel (persistent FP32 GMRES of the local systems: local matvecs + Gram-Schmidt)", npg,
-               pg_ms, pg_flops, fp32_simt_peak_tflops(sm_max),
-               "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock (MEASURED_PEAKS.json has no FP32 entry)")
-    # the dominant contraction kernel of the step (by device time) carries the roofline
+               pg_ms, pg_flops, peaks["fp32_fma"], src_fma + ", FP32", ms_step)
     roofs = sorted([(gemm_ms, r64), (gemm32_ms, r32), (gemmtc_ms, rtc), (pg_ms, rpg)], key=lambda t: -t[0])
     line["roofline"] = roofs[0][1]
-    line["roofline_other_gemm"] = [r for t, r in roofs[1:] if r["launches"]]
+    line["roofline_other"] = [r for _, r in roofs[1:] if r["launches"]]
     line["contraction_tflops_step"] = cflops / max(args.steps, 1) / (ms_step * 1e-3) / 1e12
     line["clocks"] = clk.summary()
     if not args.no_cpu_baseline:
-        r, dt = oracle_reference(p, threads=os.cpu_count() or 1, tol=1e-10)
-        kref = r["k"]
-        t_ok, it_ok = first_within(res["k_hist"], res["t_hist"], kref)
-        line["k_oracle"] = kref
-        line["k_rel_err"] = abs(res["k"] - kref) / kref
-        line["time_to_1e-6_ms"] = t_ok
-        ks = r["k_hist"]
-        n_ok = next(i for i in range(len(ks)) if np.all(np.abs(ks[i:] - kref) / kref < 1e-6)) + 1
-        line["cpu_baseline"] = {"value": dt * n_ok / max(r["iters"], 1), "unit": UNIT,
-                                "cores": os.cpu_count() or 1, "kind": "oracle",
-                                "sample": f"full FP64 power iteration ({r['iters']} iterations, {dt:.2f} s); "
-                                          f"time scaled to the first of {n_ok} iterates within 1e-6"}
+        cores = os.cpu_count() or 1
+        it_all = max(2, min(10, int(20.0 / max(1e-9, 4e-9 * p.G * p.L * p.n ** 3))))
+        t_all = oracle_sample(p, it_all, cores)
+        t_one = oracle_sample(p, 1, 1)
+        line["cpu_baseline"] = {
+            "value": t_all * n_ok_oracle, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": (f"{it_all} oracle power iterations timed on {cores} cores ({t_all:.3f} s each), scaled to "
+                       f"the {n_ok_oracle} iterations after which the oracle's k stays within 1e-6 of its "
+                       f"converged value"),
+            "cpu_model": cpu_model(),
+            "one_core": {"value": t_one * n_ok_oracle, "unit": UNIT, "cores": 1,
+                         "sample": f"1 iteration timed on 1 core ({t_one:.3f} s), scaled likewise"}}
     print(json.dumps(line))
 
 

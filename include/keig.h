@@ -111,6 +111,18 @@ int tt_ctx_gemmtc_stats(tt_ctx *ctx, int64_t *launches, double *ms, double *flop
  * 2 n r0 r1 (r0 R1 + n R1 R2 + r1 R2) each plus the Gram-Schmidt passes. */
 int tt_ctx_gmres_stats(tt_ctx *ctx, int64_t *launches, double *ms, double *flops);
 
+/* The FP32 contraction GEMM of the mixed-precision local solves, exposed so
+ * that it can be checked directly: C[b] = alpha op(A[b]) op(B[b]) + beta C[b]
+ * for b < batch, row-major, op = transpose when ta / tb != 0, device
+ * pointers, batch strides sA, sB, sC (elements).  kind: 0 the FP32 SIMT GEMM
+ * (TT_FP32_REFINED), 1 the tcgen05 TF32 three-term split (TT_TF32_SPLIT),
+ * 2 the tcgen05 BF16 three-term split (TT_BF16_SPLIT).  Enqueued on the
+ * context stream; kinds 1 and 2 synchronise to read the bounded-wait flag
+ * (TT_ETIMEOUT if an MMA wait gave up). */
+int tt_gemm_f32(tt_ctx *ctx, int kind, int ta, int tb, int M, int N, int K, float alpha, const float *A, int lda,
+                long long sA, const float *B, int ldb, long long sB, float beta, float *C, int ldc, long long sC,
+                int batch);
+
 /* Peak fused-multiply-add rate of the current device in flop/s (FP64 when
  * fp64 != 0, else FP32): four CTAs of 256 threads per SM each run eight
  * independent FMA chains for 16 x iters rounds; the best of `reps` timed
@@ -215,7 +227,10 @@ typedef enum {
   TT_TF32_SPLIT = 1,  /* linear solves: as TT_FP32_REFINED, with the Krylov contractions on the tcgen05
                          tensor cores (kind::tf32, FP32 accumulation in tensor memory) with the
                          three-term split A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi */
-  TT_BF16_SPLIT = 2,  /* reserved: contractions on tensor cores (not built) */
+  TT_BF16_SPLIT = 2,  /* linear solves: as TT_TF32_SPLIT with BF16 operands (tcgen05 kind::f16, FP32
+                         accumulation in tensor memory): x = hi + lo with hi = bf16(x), lo = bf16(x - hi),
+                         A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi (about 16 significant bits per product);
+                         the FP32 correction solves stop at 3e-5 and the FP64 refinement finishes */
   TT_FP32_REFINED = 3 /* linear solves: Krylov iterations of each local system with FP32 contractions,
                          wrapped in FP64 iterative refinement (FP64 residual, FP32 correction solve,
                          one persistent GMRES kernel per correction) until the FP64 residual meets

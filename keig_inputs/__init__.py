@@ -329,6 +329,16 @@ def config(idx: int, bc: str = "vacuum") -> Problem:
     raise ValueError(idx)
 
 
+def bare_cube(l: int, G: int = 2, order: int = 4, side: float = 10.0, seed: int = 1000) -> Problem:
+    """Bare homogeneous cube with vacuum faces, the geometry of the paper's
+    3-D benchmark (Sec. 4.2: a 10 cm cube at 128-512 grid points per axis),
+    with the seeded synthetic cross sections of config 0 (the benchmark's
+    256-group nuclear data is not available)."""
+    p = homogeneous(l=l, G=G, order=order, side=side, seed=seed,
+                    name=f"cube{1 << l}_g{G}_s{order}_{side:g}cm")
+    return p
+
+
 def random_rank1_cores(modes, seed: int, lo=0.5, hi=1.5) -> List[np.ndarray]:
     """Seeded positive rank-1 TT cores (shape (1, n_k, 1)) used as the random
     initial guess of the fixed-point iteration."""

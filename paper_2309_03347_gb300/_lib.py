@@ -14,6 +14,7 @@ TT_MV_EXACT, TT_MV_AMEN = 0, 1
 TT_FP64 = 0
 TT_FP32_REFINED = 3
 TT_TF32_SPLIT = 1
+TT_BF16_SPLIT = 2
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_FILE = os.path.join(_HERE, "_build", "libkeig_tt.so")
@@ -82,6 +83,9 @@ def load():
             "tt_ctx_reset_counters": ([P], C.c_int),
             "tt_ctx_set_wait_limit": ([P, C.c_longlong], C.c_int),
             "tt_measure_fma_peak": ([P, C.c_int, C.c_int, C.c_int, D], C.c_int),
+            "tt_gemm_f32": ([P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_float, P, C.c_int,
+                             C.c_longlong, P, C.c_int, C.c_longlong, C.c_float, P, C.c_int, C.c_longlong, C.c_int],
+                            C.c_int),
             "tt_ctx_set_profiling": ([P, C.c_int], C.c_int),
             "tt_ctx_gemm_stats": ([P, C.POINTER(C.c_int64), D, D], C.c_int),
             "tt_ctx_gemm32_stats": ([P, C.POINTER(C.c_int64), D, D], C.c_int),
@@ -797,3 +801,22 @@ def tt_measure_fma_peak(fp64: bool, iters: int = 4096, reps: int = 5, stream=Non
     if rc != TT_OK:
         raise KeigError(rc, "tt_measure_fma_peak failed")
     return float(out.value)
+
+
+def tt_gemm_f32(ctx: Context, kind: int, ta: bool, tb: bool, a, b, out, alpha: float = 1.0, beta: float = 0.0) -> None:
+    """out[i] = alpha op(a[i]) op(b[i]) + beta out[i] on float32 CUDA tensors of
+    shape (batch, rows, cols) (keig.h tt_gemm_f32; kind 0 SIMT, 1 TF32 split,
+    2 BF16 split).  Sizes are checked here before the call."""
+    import torch
+    for t in (a, b, out):
+        if not (t.is_cuda and t.dtype == torch.float32 and t.dim() == 3 and t.is_contiguous()):
+            raise KeigError(TT_EINVAL, "tt_gemm_f32: expects contiguous float32 CUDA tensors (batch, rows, cols)")
+    batch = a.shape[0]
+    M, K = (a.shape[2], a.shape[1]) if ta else (a.shape[1], a.shape[2])
+    Kb, N = (b.shape[2], b.shape[1]) if tb else (b.shape[1], b.shape[2])
+    if b.shape[0] != batch or out.shape[0] != batch or Kb != K or tuple(out.shape[1:]) != (M, N):
+        raise KeigError(TT_EINVAL, "tt_gemm_f32: inconsistent shapes")
+    vp = lambda t: C.c_void_p(t.data_ptr())
+    ctx.check(ctx.lib.tt_gemm_f32(ctx.h, int(kind), int(bool(ta)), int(bool(tb)), M, N, K, float(alpha), vp(a),
+                                  a.shape[2], a.shape[1] * a.shape[2], vp(b), b.shape[2], b.shape[1] * b.shape[2],
+                                  float(beta), vp(out), out.shape[2], out.shape[1] * out.shape[2], batch))

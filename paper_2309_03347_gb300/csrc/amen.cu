@@ -47,15 +47,22 @@ void local_matvec(Ctx *c, const double *PhiL, const double *Aajib, const double 
 // tc selects the tcgen05 TF32 three-term GEMM instead of the FP32 SIMT GEMM
 void local_matvec32(Ctx *c, const float *PhiL, const float *Aajib, const float *PhiR, const float *x, int ry1,
                     int R1, int rx1, int m, int n, int R2, int ry2, int rx2, float *y, DBuf &T1, DBuf &T2,
-                    bool tc = false) {
+                    int tc = 0) {
   T1.ensure(c, ((size_t)ry1 * R1 * n * rx2 + 1) / 2);
   T2.ensure(c, ((size_t)ry1 * m * R2 * rx2 + 1) / 2);
   float *t1 = reinterpret_cast<float *>(T1.p()), *t2 = reinterpret_cast<float *>(T2.p());
-  auto g = tc ? gemm_f32_tc : gemm_f32;
-  g(c, false, false, ry1 * R1, n * rx2, rx1, 1.f, PhiL, rx1, 0, x, n * rx2, 0, 0.f, t1, n * rx2, 0, 1);
-  g(c, true, false, m * R2, rx2, R1 * n, 1.f, Aajib, m * R2, 0, t1, rx2, (long long)R1 * n * rx2, 0.f, t2, rx2,
+  // tc: 0 FP32 SIMT GEMM, 1 tcgen05 TF32 three-term split, 2 tcgen05 BF16 three-term split
+  auto g = [&](bool ta, bool tb, int M, int N, int K, float al, const float *A, int lda, long long sA, const float *B,
+               int ldb, long long sB, float be, float *C, int ldc, long long sC, int batch) {
+    if (tc)
+      gemm_f32_tc(c, ta, tb, M, N, K, al, A, lda, sA, B, ldb, sB, be, C, ldc, sC, batch, tc == 2);
+    else
+      gemm_f32(c, ta, tb, M, N, K, al, A, lda, sA, B, ldb, sB, be, C, ldc, sC, batch);
+  };
+  g(false, false, ry1 * R1, n * rx2, rx1, 1.f, PhiL, rx1, 0, x, n * rx2, 0, 0.f, t1, n * rx2, 0, 1);
+  g(true, false, m * R2, rx2, R1 * n, 1.f, Aajib, m * R2, 0, t1, rx2, (long long)R1 * n * rx2, 0.f, t2, rx2,
     (long long)m * R2 * rx2, ry1);
-  g(c, false, true, ry1 * m, ry2, R2 * rx2, 1.f, t2, R2 * rx2, 0, PhiR, R2 * rx2, 0, 0.f, y, ry2, 0, 1);
+  g(false, true, ry1 * m, ry2, R2 * rx2, 1.f, t2, R2 * rx2, 0, PhiR, R2 * rx2, 0, 0.f, y, ry2, 0, 1);
   c->flops32 += contraction_flops_local(ry1, R1, rx1, n, m, R2, rx2, ry2);
 }
 
@@ -392,7 +399,8 @@ void amen_solve(Ctx *c, TTOp &Aop, const TT &b, TT &x, double eps, int rmax, int
   TT &A = Aop.t;
   Aop.prepare(c);
   if (rhs_op) rhs_op->prepare(c);
-  const bool use_tc = prec == TT_TF32_SPLIT;
+  const bool use_tc = prec == TT_TF32_SPLIT || prec == TT_BF16_SPLIT;
+  const int tc_kind = prec == TT_BF16_SPLIT ? 2 : (use_tc ? 1 : 0);
   const bool mixed = prec == TT_FP32_REFINED || use_tc;
   if (mixed) Aop.prepare32(c);
   if (use_tc) TT_CHECK_CUDA(cudaMemsetAsync(c->d_scalar + 8, 0, sizeof(int), c->stream));
@@ -484,7 +492,7 @@ void amen_solve(Ctx *c, TTOp &Aop, const TT &b, TT &x, double eps, int rmax, int
         const float *A32 = reinterpret_cast<const float *>(Aop.a_ajib32[k].p());
         auto mv32 = [&](const float *in, float *out) {
           local_matvec32(c, reinterpret_cast<const float *>(PL32.p()), A32, reinterpret_cast<const float *>(PR32.p()),
-                         in, r0, R1, r0, m, m, R2, r1, r1, out, T1, T2, use_tc);
+                         in, r0, R1, r0, m, m, R2, r1, r1, out, T1, T2, tc_kind);
         };
         r32.ensure(c, (N + 1) / 2);
         d32.ensure(c, (N + 1) / 2);
@@ -496,7 +504,8 @@ void amen_solve(Ctx *c, TTOp &Aop, const TT &b, TT &x, double eps, int rmax, int
           const double nrr = nrm2(c, r64.p(), N);
           if (!(nrr > loc_eps * nb)) break;
           d2f(c, r64.p(), reinterpret_cast<float *>(r32.p()), N, 1.0 / nrr);
-          const double tol_in = std::max(0.3 * loc_eps * nb / nrr, 2e-6);
+          // inner tolerance: the product's own accuracy bounds what the FP32 Krylov can reach
+          const double tol_in = std::max(0.3 * loc_eps * nb / nrr, prec == TT_BF16_SPLIT ? 3e-5 : 2e-6);
           if (!use_tc && c->persistent_gmres && pgmres32_fits(c, (int)N, G32.restart))
             git += pgmres32(c, reinterpret_cast<const float *>(PL32.p()), A32,
                             reinterpret_cast<const float *>(PR32.p()), r0, R1, m, R2, r1,

@@ -178,6 +178,24 @@ int tt_ctx_counters(tt_ctx *ctx, int64_t *launches, double *flops) {
   return TT_OK;
 }
 
+int tt_gemm_f32(tt_ctx *ctx, int kind, int ta, int tb, int M, int N, int K, float alpha, const float *A, int lda,
+                long long sA, const float *B, int ldb, long long sB, float beta, float *C, int ldc, long long sC,
+                int batch) {
+  return guarded(ctx, [&] {
+    tt::Ctx *c = &ctx->c;
+    TT_REQUIRE(kind >= 0 && kind <= 2, "tt_gemm_f32: kind must be 0, 1 or 2");
+    TT_REQUIRE(A && B && C && M >= 0 && N >= 0 && K >= 0 && batch >= 1, "tt_gemm_f32: bad arguments");
+    TT_REQUIRE(lda >= (ta ? M : K) && ldb >= (tb ? K : N) && ldc >= N, "tt_gemm_f32: leading dimension too small");
+    if (kind == 0) {
+      tt::gemm_f32(c, ta != 0, tb != 0, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch);
+      return;
+    }
+    TT_CHECK_CUDA(cudaMemsetAsync(c->d_scalar + 8, 0, sizeof(int), c->stream));
+    tt::gemm_f32_tc(c, ta != 0, tb != 0, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch, kind == 2);
+    if (tt::tc_error_flag(c)) throw tt::Error(TT_ETIMEOUT, "tt_gemm_f32: a tensor-core GEMM gave up waiting");
+  });
+}
+
 int tt_ctx_set_wait_limit(tt_ctx *ctx, long long spins) {
   if (!ctx) return TT_EINVAL;
   ctx->c.wait_limit = spins < 0 ? -1 : spins;
@@ -446,8 +464,8 @@ int tt_solve_local(tt_ctx *ctx, const tt_op *A, const tt_vec *b, tt_vec *x, doub
   int conv = 1;
   int rc = guarded(ctx, [&] {
     TT_REQUIRE(A && b && x, "null argument");
-    TT_REQUIRE(prec == TT_FP64 || prec == TT_FP32_REFINED || prec == TT_TF32_SPLIT,
-               "tt_solve_local: prec must be TT_FP64, TT_FP32_REFINED or TT_TF32_SPLIT");
+    TT_REQUIRE(prec == TT_FP64 || prec == TT_FP32_REFINED || prec == TT_TF32_SPLIT || prec == TT_BF16_SPLIT,
+               "tt_solve_local: prec must be TT_FP64, TT_FP32_REFINED, TT_TF32_SPLIT or TT_BF16_SPLIT");
     TT_REQUIRE(eps > 0 && eps < 1, "tt_solve_local: eps in (0, 1)");
     TT_REQUIRE(max_sweeps >= 1 && kick >= 0, "tt_solve_local: bad sweeps/kick");
     tt_op *Am = const_cast<tt_op *>(A);
@@ -526,8 +544,9 @@ using clk = std::chrono::steady_clock;
 
 void check_opts(const keig_opts *opts) {
   TT_REQUIRE(opts, "null options");
-  TT_REQUIRE(opts->prec == TT_FP64 || opts->prec == TT_FP32_REFINED || opts->prec == TT_TF32_SPLIT,
-             "keig: prec must be TT_FP64, TT_FP32_REFINED or TT_TF32_SPLIT");
+  TT_REQUIRE(opts->prec == TT_FP64 || opts->prec == TT_FP32_REFINED || opts->prec == TT_TF32_SPLIT ||
+                 opts->prec == TT_BF16_SPLIT,
+             "keig: prec must be TT_FP64, TT_FP32_REFINED, TT_TF32_SPLIT or TT_BF16_SPLIT");
   TT_REQUIRE(opts->eps > 0 && opts->eps < 1 && opts->max_iter >= 1, "keig: bad eps/max_iter");
   TT_REQUIRE(opts->scheme == 0 || opts->scheme == 1, "keig: scheme must be 0 or 1");
   TT_REQUIRE(opts->mv_kind == 0 || opts->mv_kind == 1, "keig: mv_kind must be 0 or 1");

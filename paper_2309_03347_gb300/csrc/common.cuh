@@ -173,9 +173,11 @@ bool has_nonfinite(Ctx *c, const double *x, size_t n);
 // FP32 counterparts used by the mixed-precision local solves
 void gemm_f32(Ctx *c, bool ta, bool tb, int M, int N, int K, float alpha, const float *A, int lda, long long sA,
               const float *B, int ldb, long long sB, float beta, float *C, int ldc, long long sC, int batch = 1);
-// the same product on the tcgen05 tensor cores (kind::tf32, three-term split; tc_gemm.cu)
+// the same product on the tcgen05 tensor cores with the three-term split
+// (tc_gemm.cu): kind::tf32, or kind::f16 with BF16 operands when bf16
 void gemm_f32_tc(Ctx *c, bool ta, bool tb, int M, int N, int K, float alpha, const float *A, int lda, long long sA,
-                 const float *B, int ldb, long long sB, float beta, float *C, int ldc, long long sC, int batch = 1);
+                 const float *B, int ldb, long long sB, float beta, float *C, int ldc, long long sC, int batch = 1,
+                 bool bf16 = false);
 // nonzero when a tensor-core GEMM gave up a bounded wait (reads device memory)
 int tc_error_flag(Ctx *c);
 void d2f(Ctx *c, const double *x, float *y, size_t n, double s = 1.0);

@@ -1,6 +1,9 @@
-// FP32 GEMM on the 5th-generation tensor cores (tcgen05, kind::tf32) with a
-// three-term split: each FP32 operand x = hi + lo with hi its TF32 truncation;
-// A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi, accumulated in FP32 in tensor memory.
+// FP32 GEMM on the 5th-generation tensor cores (tcgen05) with a three-term
+// split: each FP32 operand x = hi + lo, A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi,
+// accumulated in FP32 in tensor memory.  Two operand formats: kind::tf32 (hi
+// the TF32 truncation of x, lo = x - hi exactly representable: about 21
+// significant bits) and kind::f16 with BF16 operands (hi = bf16(x), lo =
+// bf16(x - hi): about 16 significant bits).  A and B always share the format.
 // One CTA of 128 threads owns a 128 x 64 output tile of one (batch, K-split)
 // pair; K advances in chunks of 32 through two shared-memory stages in the
 // canonical K-major no-swizzle layout (8-row x 16-byte core matrices), so the
@@ -15,7 +18,8 @@ namespace tc {
 
 constexpr int TM = 128;  // tile rows (MMA M)
 constexpr int TN = 64;   // tile columns (MMA N)
-constexpr int TK = 32;   // K per shared-memory stage (4 MMAs of K = 8)
+constexpr int TK = 32;   // FP32 K per shared-memory stage (4 MMAs of K = 8); BF16 stages hold 2 x TK
+constexpr int ROW_BYTES = 128;  // bytes of K per operand row and stage (both formats)
 constexpr int THREADS = 128;
 // byte sizes of one operand buffer
 constexpr int A_BYTES = TM * TK * 4;  // 16 KB
@@ -47,6 +51,11 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
 __host__ __device__ constexpr uint32_t idesc_tf32(int m, int n) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
+// instruction descriptor of kind::f16 with BF16 A and B (the same type for
+// both operands), D F32, both K-major
+__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
 
 constexpr long long WAIT_LIMIT = 1LL << 20;
 
@@ -73,19 +82,38 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t adesc, uint64_t
       : "memory");
 }
 
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+      :
+      : "r"(tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
 __device__ __forceinline__ float tf32_hi(float v) { return __uint_as_float(__float_as_uint(v) & 0xFFFFE000u); }
 
-// Stage an R x TK operand tile (rows row0.., K columns k0..) as hi and lo
-// parts.  Element (r, k) is p[r * ld + k] when KCONTIG, else p[k * ld + r];
-// rows >= nrows and columns >= kend read as zero.  Each thread moves units of
-// four consecutive k of one row (one 16-byte core-matrix row); the unit order
-// puts 8 lanes on one whole core matrix, so the 16-byte shared stores do not
-// conflict, and the global reads run along the contiguous index.
-template <bool KCONTIG, int R>
+// BF16 bits of x rounded to nearest even (finite inputs), and back to FP32
+__device__ __forceinline__ uint32_t bf16_bits(float x) {
+  const uint32_t u = __float_as_uint(x);
+  return (u + 0x7FFFu + ((u >> 16) & 1u)) >> 16;
+}
+__device__ __forceinline__ float bf16_val(uint32_t b) { return __uint_as_float(b << 16); }
+
+// Stage an R-row operand tile (rows row0.., K columns k0.. : TK columns in
+// FP32, 2 TK in BF16, 128 bytes per row either way) as hi and lo parts.
+// Element (r, k) is p[r * ld + k] when KCONTIG, else p[k * ld + r]; rows >=
+// nrows and columns >= kend read as zero.  Each thread moves units of one
+// 16-byte core-matrix row (four FP32 or eight BF16 consecutive k of one row);
+// the unit order puts 8 lanes on one whole core matrix, so the 16-byte shared
+// stores do not conflict, and the global reads run along the contiguous index.
+template <bool KCONTIG, int R, bool BF16>
 __device__ __forceinline__ void stage_operand(const float *__restrict__ p, int ld, int row0, int nrows, int k0,
                                               int kend, uint8_t *hi, uint8_t *lo, int tid) {
+  constexpr int EPU = BF16 ? 8 : 4;  // elements per 16-byte unit
 #pragma unroll 2
-  for (int u = tid; u < R * TK / 4; u += THREADS) {
+  for (int u = tid; u < R * 8; u += THREADS) {
     int r, kg;
     if (KCONTIG) {
       r = ((u >> 6) << 3) | (u & 7);
@@ -95,24 +123,37 @@ __device__ __forceinline__ void stage_operand(const float *__restrict__ p, int l
       kg = u / R;
     }
     const int gr = row0 + r;
-    float v[4];
+    float v[EPU];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int gk = k0 + 4 * kg + i;
+    for (int i = 0; i < EPU; ++i) {
+      const int gk = k0 + EPU * kg + i;
       v[i] = (gr < nrows && gk < kend) ? (KCONTIG ? p[(long long)gr * ld + gk] : p[(long long)gk * ld + gr]) : 0.f;
     }
-    float4 h, l;
-    h.x = tf32_hi(v[0]);
-    h.y = tf32_hi(v[1]);
-    h.z = tf32_hi(v[2]);
-    h.w = tf32_hi(v[3]);
-    l.x = v[0] - h.x;
-    l.y = v[1] - h.y;
-    l.z = v[2] - h.z;
-    l.w = v[3] - h.w;
-    const uint32_t off = kmajor_offset(r, 4 * kg, R);
-    *reinterpret_cast<float4 *>(hi + off) = h;
-    *reinterpret_cast<float4 *>(lo + off) = l;
+    const uint32_t off = (uint32_t)(((kg * (R >> 3) + (r >> 3)) << 7) + ((r & 7) << 4));
+    if (BF16) {
+      uint32_t h[4], l[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const uint32_t h0 = bf16_bits(v[2 * i]), h1 = bf16_bits(v[2 * i + 1]);
+        const uint32_t l0 = bf16_bits(v[2 * i] - bf16_val(h0)), l1 = bf16_bits(v[2 * i + 1] - bf16_val(h1));
+        h[i] = h0 | (h1 << 16);  // lower k in the lower half-word
+        l[i] = l0 | (l1 << 16);
+      }
+      *reinterpret_cast<uint4 *>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+      *reinterpret_cast<uint4 *>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
+    } else {
+      float4 h, l;
+      h.x = tf32_hi(v[0]);
+      h.y = tf32_hi(v[1]);
+      h.z = tf32_hi(v[2]);
+      h.w = tf32_hi(v[3]);
+      l.x = v[0] - h.x;
+      l.y = v[1] - h.y;
+      l.z = v[2] - h.z;
+      l.w = v[3] - h.w;
+      *reinterpret_cast<float4 *>(hi + off) = h;
+      *reinterpret_cast<float4 *>(lo + off) = l;
+    }
   }
 }
 
@@ -120,7 +161,7 @@ __device__ __forceinline__ void stage_operand(const float *__restrict__ p, int l
 // z = blockIdx.z = b * ksplit + q (row-major FP32; op(A) is M x K, op(B) K x N).
 // Split q covers K indices [q * kchunk, min(K, (q + 1) * kchunk)).
 // lbo / sbo: byte offsets of the operand descriptors (K-adjacent / row-adjacent core matrices).
-template <bool TA, bool TB>
+template <bool TA, bool TB, bool BF16>
 __global__ void __launch_bounds__(THREADS) tc_gemm_kernel(int M, int N, int K, int kchunk, int ksplit, float alpha,
                                                           const float *__restrict__ A, int lda, long long sA,
                                                           const float *__restrict__ B, int ldb, long long sB,
@@ -137,7 +178,8 @@ __global__ void __launch_bounds__(THREADS) tc_gemm_kernel(int M, int N, int K, i
   B += bz * sB;
   C += z * sC;
   const int kbeg = q * kchunk, kend = min(K, kbeg + kchunk);
-  const int nch = kend > kbeg ? (kend - kbeg + TK - 1) / TK : 0;
+  constexpr int TKE = BF16 ? 2 * TK : TK;  // K elements per stage
+  const int nch = kend > kbeg ? (kend - kbeg + TKE - 1) / TKE : 0;
   const uint32_t s_base = (uint32_t)__cvta_generic_to_shared(smem);
   uint32_t mb[STAGES];
 #pragma unroll
@@ -158,7 +200,7 @@ __global__ void __launch_bounds__(THREADS) tc_gemm_kernel(int M, int N, int K, i
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base_sh;
-  const uint32_t idesc = idesc_tf32(TM, TN);
+  const uint32_t idesc = BF16 ? idesc_bf16(TM, TN) : idesc_tf32(TM, TN);
   // per stage: commits issued and commit waits completed (uniform over the CTA);
   // a stage has at most one commit outstanding, whose phase parity is waits & 1
   int commits[STAGES] = {0, 0}, waits[STAGES] = {0, 0};
@@ -174,23 +216,29 @@ __global__ void __launch_bounds__(THREADS) tc_gemm_kernel(int M, int N, int K, i
     }
     uint8_t *st = smem + s * STAGE_BYTES;
     uint8_t *a_hi = st, *a_lo = st + A_BYTES, *b_hi = st + 2 * A_BYTES, *b_lo = st + 2 * A_BYTES + B_BYTES;
-    const int k0 = kbeg + ch * TK;
-    stage_operand<!TA, TM>(A, lda, m0, M, k0, kend, a_hi, a_lo, tid);
-    stage_operand<TB, TN>(B, ldb, n0, N, k0, kend, b_hi, b_lo, tid);
+    const int k0 = kbeg + ch * TKE;
+    stage_operand<!TA, TM, BF16>(A, lda, m0, M, k0, kend, a_hi, a_lo, tid);
+    stage_operand<TB, TN, BF16>(B, ldb, n0, N, k0, kend, b_hi, b_lo, tid);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t sa = s_base + s * STAGE_BYTES, sb = sa + 2 * A_BYTES;
 #pragma unroll
-      for (int j = 0; j < TK / 8; ++j) {
-        // K slice [8j, 8j + 8): core-matrix columns 2j and 2j + 1
+      for (int j = 0; j < ROW_BYTES / 32; ++j) {
+        // 32 bytes of K per MMA (8 TF32 or 16 BF16): core-matrix columns 2j and 2j + 1
         const uint32_t ao = (uint32_t)(2 * j * (TM / 8)) * 128u, bo = (uint32_t)(2 * j * (TN / 8)) * 128u;
         const uint64_t dah = smem_desc(sa + ao, a_lbo, a_sbo), dal = smem_desc(sa + A_BYTES + ao, a_lbo, a_sbo);
         const uint64_t dbh = smem_desc(sb + bo, b_lbo, b_sbo), dbl = smem_desc(sb + B_BYTES + bo, b_lbo, b_sbo);
-        mma_tf32(tmem, dah, dbh, idesc, (ch > 0 || j > 0) ? 1u : 0u);
-        mma_tf32(tmem, dah, dbl, idesc, 1u);
-        mma_tf32(tmem, dal, dbh, idesc, 1u);
+        if (BF16) {
+          mma_bf16(tmem, dah, dbh, idesc, (ch > 0 || j > 0) ? 1u : 0u);
+          mma_bf16(tmem, dah, dbl, idesc, 1u);
+          mma_bf16(tmem, dal, dbh, idesc, 1u);
+        } else {
+          mma_tf32(tmem, dah, dbh, idesc, (ch > 0 || j > 0) ? 1u : 0u);
+          mma_tf32(tmem, dah, dbl, idesc, 1u);
+          mma_tf32(tmem, dal, dbh, idesc, 1u);
+        }
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb[s])
                    : "memory");
