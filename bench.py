@@ -41,14 +41,15 @@ METRIC = "time to k within 1e-6 of FP64 oracle; TT contraction TFLOP/s and % of 
 UNIT = "s"
 GOLDEN = os.path.join(ROOT, "tests", "golden", "oracle_reference.txt")
 
-# name -> (problem, rank cap, eps, local form (0 Galerkin, 1 least squares), note)
+# name -> (problem, rank cap, eps, local form (0 Galerkin, 1 least squares),
+#          AMEn sweeps per product and per solve, note)
 WORKLOADS = {
-    "cube128_g2_s4_10cm": (lambda: ki.bare_cube(7), 64, 1e-8, 1,
+    "cube128_g2_s4_10cm": (lambda: ki.bare_cube(7), 96, 1e-8, 1, 1,
                            "bare homogeneous 10 cm cube, 128^3 grid points (the paper's Sec. 4.2 geometry at its "
                            "smallest grid), 2 groups, S4 level-symmetric (24 directions), vacuum"),
-    "cube64_g2_s4_10cm": (lambda: ki.bare_cube(6), 64, 1e-8, 1,
+    "cube64_g2_s4_10cm": (lambda: ki.bare_cube(6), 96, 1e-8, 1, 1,
                           "bare homogeneous 10 cm cube, 64^3 grid points, 2 groups, S4, vacuum"),
-    "box32_g4_s8": (lambda: ki.config(1), 64, 1e-7, 0,
+    "box32_g4_s8": (lambda: ki.config(1), 64, 1e-7, 0, 2,
                     "fissile box in a c = 0.9 reflector, 32^3, 4 groups, S8 (its rank cap 64 limits k to about "
                     "5e-5 of the oracle: this workload cannot reach 1e-6)"),
 }
@@ -201,11 +202,11 @@ def measured_peaks(K):
 
 
 def make_opts(K, name, prec, max_iter):
-    _, cap, eps, lf, _ = WORKLOADS[name]
+    _, cap, eps, lf, sweeps, _ = WORKLOADS[name]
     o = K.keig_default_opts()
     o.eps, o.rmax = eps, cap
     o.tol_k, o.tol_psi, o.max_iter = 1e-10, 1e-7, max_iter
-    o.solve_sweeps, o.mv_sweeps, o.kick = 2, 2, 4
+    o.solve_sweeps, o.mv_sweeps, o.kick = sweeps, sweeps, 4
     o.scheme = 0
     o.local_form = lf
     o.prec = {"mixed": K.TT_FP32_REFINED, "tf32": K.TT_TF32_SPLIT, "bf16": K.TT_BF16_SPLIT,
@@ -353,7 +354,7 @@ def main():
     if rank != 0:
         return
     res = results[-1]
-    _, cap, eps, lf, note = WORKLOADS[name]
+    _, cap, eps, lf, sweeps, note = WORKLOADS[name]
     line = {
         "metric": METRIC, "value": ms_step / 1e3, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
@@ -361,6 +362,7 @@ def main():
         "config": {"workload": name, "description": note, "grid": f"{p.n}^3", "groups": p.G, "directions": p.L,
                    "side_cm": p.side[0], "rank_cap": cap, "eps": eps, "scheme": "paper",
                    "local_systems": "least squares (Eq. (linear_system_obj))" if lf else "Galerkin",
+                   "amen_sweeps": sweeps,
                    "outer_iterations": n_it, "precision": PRECISION_TEXT[args.prec],
                    "l2": "flushed between steps (256 MB write)",
                    "parallelism": "replicas" if world > 1 else "single"},

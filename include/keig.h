@@ -269,12 +269,26 @@ int tt_matvec(tt_ctx *ctx, const tt_op *A, const tt_vec *x, double scale, int me
  * names): the local systems are Galerkin projections onto the current
  * interfaces, solved by restarted GMRES to eps/sqrt(d); the local solution is
  * split by a truncated SVD (threshold eps/sqrt(d), cap rmax) and enriched
- * with a rank-`kick` residual direction.  x: initial guess on entry, solution
+ * with a rank-`kick` residual direction (kick = 0: one-site ALS, no
+ * enrichment).  x: initial guess on entry, solution
  * on return.  sweeps_done / rel_change (may be NULL): sweeps run and the
  * largest relative change of a local solution in the last sweep.
  * TT_ENOCONV when max_sweeps ran out (x still holds the last iterate). */
 int tt_solve_local(tt_ctx *ctx, const tt_op *A, const tt_vec *b, tt_vec *x, double eps, int rmax,
                    int max_sweeps, int kick, tt_prec prec, int *sweeps_done, double *rel_change);
+
+/* Solve A x = b by two-site DMRG sweeps (the two-site member of the
+ * alternating family of Sec. 3.5: all cores fixed but a neighbouring pair):
+ * for each bond the Galerkin local system of the merged supercore (modes
+ * n_k n_{k+1}) is solved by the local solver of tt_solve_local (GMRES in FP64
+ * or the FP32-refined / tensor-core forms of prec) and split back by a
+ * truncated SVD (threshold eps/sqrt(d), cap rmax), which adapts the ranks
+ * without enrichment.  The merged operator core holds R_k (n_k n_{k+1})^2
+ * R_{k+2} doubles, so the method suits moderate mode sizes.  x: initial guess
+ * on entry, solution on return.  TT_ENOCONV when the largest relative change
+ * of a supercore is still >= eps after max_sweeps sweeps. */
+int tt_solve_dmrg(tt_ctx *ctx, const tt_op *A, const tt_vec *b, tt_vec *x, double eps, int rmax, int max_sweeps,
+                  tt_prec prec, int *sweeps_done, double *rel_change);
 
 /* ---------------------------------------------------------------- the eigen loop */
 
@@ -302,6 +316,10 @@ typedef struct {
                           indefinite, so a Galerkin projection of H onto rank-capped frames can
                           be singular; N's projections are symmetric positive definite.
                         Applies to keig_fixed_point (other entry points use 0). */
+  int solve_method;  /* the alternating method of the linear solve (Sec. 3.5, "ALS, DMRG, AMEn"):
+                        0 AMEn (one site, residual enrichment of rank kick); 1 ALS (one site, no
+                        enrichment: ranks never grow above those of the initial guess);
+                        2 two-site DMRG (tt_solve_dmrg; Galerkin local systems only) */
 } keig_opts;
 
 typedef struct {
@@ -316,7 +334,7 @@ typedef struct {
 
 /* Fill opts with defaults (eps 1e-7, rmax 64, tol_k 1e-9, tol_psi 1e-5,
  * max_iter 400, solve_sweeps 2, mv_sweeps 2, kick 4, scheme 0, FP64,
- * eps_op 1e-12, AMEn product, Galerkin local systems). */
+ * eps_op 1e-12, AMEn product, Galerkin local systems, AMEn solve). */
 int keig_default_opts(keig_opts *opts);
 
 /* The QTT fixed point of Eq. (TT_k_eff_fixed_points):

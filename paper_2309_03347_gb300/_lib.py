@@ -49,7 +49,7 @@ class KeigOpts(C.Structure):
         ("eps", C.c_double), ("rmax", C.c_int), ("tol_k", C.c_double), ("tol_psi", C.c_double),
         ("max_iter", C.c_int), ("solve_sweeps", C.c_int), ("mv_sweeps", C.c_int), ("kick", C.c_int),
         ("scheme", C.c_int), ("prec", C.c_int), ("eps_op", C.c_double), ("psi0_cores", D),
-        ("mv_kind", C.c_int), ("local_form", C.c_int),
+        ("mv_kind", C.c_int), ("local_form", C.c_int), ("solve_method", C.c_int),
     ]
 
 
@@ -113,6 +113,7 @@ def load():
             "tt_matvec": ([P, P, P, C.c_double, C.c_int, C.c_double, C.c_int, C.c_int, C.c_int, C.POINTER(P)],
                           C.c_int),
             "tt_solve_local": ([P, P, P, P, C.c_double, C.c_int, C.c_int, C.c_int, C.c_int, I, D], C.c_int),
+            "tt_solve_dmrg": ([P, P, P, P, C.c_double, C.c_int, C.c_int, C.c_int, I, D], C.c_int),
             "keig_default_opts": ([C.POINTER(KeigOpts)], C.c_int),
             "keig_fixed_point": ([P, C.POINTER(TTProblem), C.POINTER(KeigOpts), C.POINTER(KeigResult),
                                   C.POINTER(P), D], C.c_int),
@@ -421,6 +422,18 @@ def tt_solve_local(ctx: Context, A: TTOp, b: TTVec, x: TTVec, eps: float, rmax: 
     dx = C.c_double()
     rc = ctx.lib.tt_solve_local(ctx.h, A.h, b.h, x.h, float(eps), int(rmax), int(max_sweeps), int(kick),
                                 int(prec), C.byref(sw), C.byref(dx))
+    if not (allow_noconv and rc == TT_ENOCONV):
+        ctx.check(rc)
+    return dict(sweeps=sw.value, rel_change=dx.value, code=rc)
+
+
+def tt_solve_dmrg(ctx: Context, A: TTOp, b: TTVec, x: TTVec, eps: float, rmax: int = 0,
+                  max_sweeps: int = 10, prec: int = TT_FP64, allow_noconv: bool = False):
+    """Two-site DMRG solve of A x = b (keig.h tt_solve_dmrg); x: guess in, solution out."""
+    sw = C.c_int()
+    dx = C.c_double()
+    rc = ctx.lib.tt_solve_dmrg(ctx.h, A.h, b.h, x.h, float(eps), int(rmax), int(max_sweeps), int(prec),
+                               C.byref(sw), C.byref(dx))
     if not (allow_noconv and rc == TT_ENOCONV):
         ctx.check(rc)
     return dict(sweeps=sw.value, rel_change=dx.value, code=rc)

@@ -333,6 +333,66 @@ int gmres32(Ctx *c, Gmres32 &G, MV &&mv, const float *b, float *x, size_t N, dou
   }
 }
 
+// The local system of one core (or of a merged pair of cores): Galerkin
+// projection (Phi_L, A, Phi_R) with square ranks r0 x m x r1, solved to the
+// relative residual tol from the initial guess in sol.  FP64 GMRES, or FP32
+// Krylov corrections inside FP64 iterative refinement (TT_FP32_REFINED: SIMT
+// contractions, one persistent GMRES kernel per correction when it fits;
+// TT_TF32_SPLIT / TT_BF16_SPLIT: tcgen05 contractions).  A32: FP32 copy of the
+// operator core (a_ajib layout) for the mixed precisions.
+struct LocalSolver {
+  Gmres G;
+  Gmres32 G32;
+  PGWork PGW;
+  DBuf PL32, PR32, r32, d32, r64, T1, T2;
+
+  long long solve(Ctx *c, int prec, const double *PL, const double *A, const float *A32, const double *PR, int r0,
+                  int R1, int m, int R2, int r1, const double *rhs, double *sol, double tol) {
+    const size_t N = (size_t)r0 * m * r1;
+    auto mv = [&](const double *in, double *out) {
+      local_matvec(c, PL, A, PR, in, r0, R1, r0, m, m, R2, r1, r1, out, T1, T2);
+    };
+    const bool use_tc = prec == TT_TF32_SPLIT || prec == TT_BF16_SPLIT;
+    const int tc_kind = prec == TT_BF16_SPLIT ? 2 : (use_tc ? 1 : 0);
+    if (prec == TT_FP64) {
+      PhaseTimer pt(c, "solve.gmres");
+      return gmres(c, G, mv, rhs, sol, N, tol);
+    }
+    // iterative refinement: FP64 residual, FP32 GMRES for the correction
+    PhaseTimer pt(c, "solve.gmres_mixed");
+    long long git = 0;
+    const size_t nl = (size_t)r0 * R1 * r0, nr = (size_t)r1 * R2 * r1;
+    PL32.ensure(c, (nl + 1) / 2);
+    PR32.ensure(c, (nr + 1) / 2);
+    float *pl32 = reinterpret_cast<float *>(PL32.p()), *pr32 = reinterpret_cast<float *>(PR32.p());
+    d2f(c, PL, pl32, nl);
+    d2f(c, PR, pr32, nr);
+    auto mv32 = [&](const float *in, float *out) {
+      local_matvec32(c, pl32, A32, pr32, in, r0, R1, r0, m, m, R2, r1, r1, out, T1, T2, tc_kind);
+    };
+    r32.ensure(c, (N + 1) / 2);
+    d32.ensure(c, (N + 1) / 2);
+    r64.ensure(c, N);
+    float *r32p = reinterpret_cast<float *>(r32.p()), *d32p = reinterpret_cast<float *>(d32.p());
+    const double nb = nrm2(c, rhs, N);
+    for (int ref = 0; ref < 6 && nb > 0; ++ref) {
+      mv(sol, r64.p());
+      axpby(c, N, 1.0, rhs, -1.0, r64.p());
+      const double nrr = nrm2(c, r64.p(), N);
+      if (!(nrr > tol * nb)) break;
+      d2f(c, r64.p(), r32p, N, 1.0 / nrr);
+      // inner tolerance: the product's own accuracy bounds what the FP32 Krylov can reach
+      const double tol_in = std::max(0.3 * tol * nb / nrr, prec == TT_BF16_SPLIT ? 3e-5 : 2e-6);
+      if (!use_tc && c->persistent_gmres && pgmres32_fits(c, (int)N, G32.restart))
+        git += pgmres32(c, pl32, A32, pr32, r0, R1, m, R2, r1, r32p, d32p, tol_in, G32.restart, G32.maxit, PGW);
+      else
+        git += gmres32(c, G32, mv32, r32p, d32p, N, tol_in);
+      f2d_axpy(c, d32p, sol, N, nrr);
+    }
+    return git;
+  }
+};
+
 struct Iface {
   std::vector<DBuf> L, R;
   void init(Ctx *c, int d) {
@@ -400,7 +460,6 @@ void amen_solve(Ctx *c, TTOp &Aop, const TT &b, TT &x, double eps, int rmax, int
   Aop.prepare(c);
   if (rhs_op) rhs_op->prepare(c);
   const bool use_tc = prec == TT_TF32_SPLIT || prec == TT_BF16_SPLIT;
-  const int tc_kind = prec == TT_BF16_SPLIT ? 2 : (use_tc ? 1 : 0);
   const bool mixed = prec == TT_FP32_REFINED || use_tc;
   if (mixed) Aop.prepare32(c);
   if (use_tc) TT_CHECK_CUDA(cudaMemsetAsync(c->d_scalar + 8, 0, sizeof(int), c->stream));
@@ -457,10 +516,8 @@ void amen_solve(Ctx *c, TTOp &Aop, const TT &b, TT &x, double eps, int rmax, int
     }
   };
   right_all();
-  Gmres G;
-  Gmres32 G32;
-  PGWork PGW;
-  DBuf rhs, sol, solt, crz, czz, tmp, PL32, PR32, r32, d32, r64;
+  LocalSolver LS;
+  DBuf rhs, sol, solt, crz, czz, tmp;
   double maxdx = 0.0;
   int swp = 0;
   long long git = 0;
@@ -474,49 +531,9 @@ void amen_solve(Ctx *c, TTOp &Aop, const TT &b, TT &x, double eps, int rmax, int
       rhs_local(k, QX.L[k].p(), QX.R[k + 1].p(), r0, r1, rhs.p());
       sol.ensure(c, N);
       copy(c, sol.p(), x.core[k].p(), N);
-      auto mv = [&](const double *in, double *out) {
-        local_matvec(c, PX.L[k].p(), Aop.a_ajib[k].p(), PX.R[k + 1].p(), in, r0, R1, r0, m, m, R2, r1, r1, out,
-                     T1, T2);
-      };
-      if (!mixed) {
-        PhaseTimer pt(c, "solve.gmres");
-        git += gmres(c, G, mv, rhs.p(), sol.p(), N, loc_eps);
-      } else {
-        // iterative refinement: FP64 residual, FP32 GMRES for the correction
-        PhaseTimer pt(c, "solve.gmres_mixed");
-        const size_t nl = (size_t)r0 * R1 * r0, nr = (size_t)r1 * R2 * r1;
-        PL32.ensure(c, (nl + 1) / 2);
-        PR32.ensure(c, (nr + 1) / 2);
-        d2f(c, PX.L[k].p(), reinterpret_cast<float *>(PL32.p()), nl);
-        d2f(c, PX.R[k + 1].p(), reinterpret_cast<float *>(PR32.p()), nr);
-        const float *A32 = reinterpret_cast<const float *>(Aop.a_ajib32[k].p());
-        auto mv32 = [&](const float *in, float *out) {
-          local_matvec32(c, reinterpret_cast<const float *>(PL32.p()), A32, reinterpret_cast<const float *>(PR32.p()),
-                         in, r0, R1, r0, m, m, R2, r1, r1, out, T1, T2, tc_kind);
-        };
-        r32.ensure(c, (N + 1) / 2);
-        d32.ensure(c, (N + 1) / 2);
-        r64.ensure(c, N);
-        const double nb = nrm2(c, rhs.p(), N);
-        for (int ref = 0; ref < 6 && nb > 0; ++ref) {
-          mv(sol.p(), r64.p());
-          axpby(c, N, 1.0, rhs.p(), -1.0, r64.p());
-          const double nrr = nrm2(c, r64.p(), N);
-          if (!(nrr > loc_eps * nb)) break;
-          d2f(c, r64.p(), reinterpret_cast<float *>(r32.p()), N, 1.0 / nrr);
-          // inner tolerance: the product's own accuracy bounds what the FP32 Krylov can reach
-          const double tol_in = std::max(0.3 * loc_eps * nb / nrr, prec == TT_BF16_SPLIT ? 3e-5 : 2e-6);
-          if (!use_tc && c->persistent_gmres && pgmres32_fits(c, (int)N, G32.restart))
-            git += pgmres32(c, reinterpret_cast<const float *>(PL32.p()), A32,
-                            reinterpret_cast<const float *>(PR32.p()), r0, R1, m, R2, r1,
-                            reinterpret_cast<const float *>(r32.p()), reinterpret_cast<float *>(d32.p()), tol_in,
-                            G32.restart, G32.maxit, PGW);
-          else
-            git += gmres32(c, G32, mv32, reinterpret_cast<const float *>(r32.p()),
-                           reinterpret_cast<float *>(d32.p()), N, tol_in);
-          f2d_axpy(c, reinterpret_cast<const float *>(d32.p()), sol.p(), N, nrr);
-        }
-      }
+      git += LS.solve(c, prec, PX.L[k].p(), Aop.a_ajib[k].p(),
+                      mixed ? reinterpret_cast<const float *>(Aop.a_ajib32[k].p()) : nullptr, PX.R[k + 1].p(), r0,
+                      R1, m, R2, r1, rhs.p(), sol.p(), loc_eps);
       // relative change of the local solution
       tmp.ensure(c, N);
       copy(c, tmp.p(), sol.p(), N);
@@ -544,6 +561,18 @@ void amen_solve(Ctx *c, TTOp &Aop, const TT &b, TT &x, double eps, int rmax, int
       solt.ensure(c, N);
       gemm(c, true, false, r0 * m, r1, rk, 1.0, s.Ut.p(), r0 * m, 0, v.p(), r1, 0, 0.0, solt.p(), r1, 0);
       const int rz0 = z.r[k], rz1 = z.r[k + 1];
+      if (kick <= 0) {
+        // one-site ALS: no residual enrichment, the truncated solution alone
+        split_enrich(c, x, k, s, rk, nullptr, 0);
+        const int nr1 = x.r[k + 1];
+        left_update(c, PX.L[k].p(), x.core[k].p(), Aop.a_ajib[k].p(), x.core[k].p(), r0, R1, r0, m, m, R2, nr1, nr1,
+                    PX.L[k + 1], T1, T2);
+        rhs_left(k, QX.L[k].p(), x.core[k].p(), r0, nr1, QX.L[k + 1]);
+        left_update(c, PZ.L[k].p(), z.core[k].p(), Aop.a_ajib[k].p(), x.core[k].p(), rz0, R1, r0, m, m, R2, rz1, nr1,
+                    PZ.L[k + 1], T1, T2);
+        rhs_left(k, QZ.L[k].p(), z.core[k].p(), rz0, rz1, QZ.L[k + 1]);
+        continue;
+      }
       PhaseTimer pt_res(c, "amen.residual");
       // crz = x'b z - x'Ax z . solt     (r0, m, rz1)
       crz.ensure(c, (size_t)r0 * m * rz1);
@@ -698,6 +727,117 @@ void amen_mv(Ctx *c, TTOp &Aop, const TT &xin, TT &y, double eps, int rmax, int 
   if (st) {
     st->sweeps = std::min(swp, nswp);
     st->max_dx = maxdx;
+  }
+}
+
+// Two-site DMRG solve of A x = b (the two-site member of the alternating
+// family Sec. 3.5 names: "fix all cores but two"): for each bond k the local
+// system of the merged supercore X_k X_{k+1} (modes n_k n_{k+1}) is projected
+// with the interfaces of the cores outside the pair (Galerkin, as the
+// one-site solve), solved by the same local solver, and split back by a
+// truncated SVD (threshold eps/sqrt(d), cap rmax), so ranks adapt without
+// residual enrichment.  The merged operator core (R_k, n n', n n', R_{k+2})
+// is formed per pair: meant for moderate mode sizes.
+void dmrg_solve(Ctx *c, TTOp &Aop, const TT &b, TT &x, double eps, int rmax, int nswp, SolveStats *st, int prec) {
+  TT &A = Aop.t;
+  Aop.prepare(c);
+  const int d = A.d;
+  TT_REQUIRE(d >= 2 && b.d == d && x.d == d, "dmrg_solve: need d >= 2 and matching dimensions");
+  for (int k = 0; k < d; ++k)
+    TT_REQUIRE(A.mo[k] == A.mi[k] && A.mi[k] == x.n[k] && b.n[k] == x.n[k], "dmrg_solve: mode mismatch");
+  const bool mixed = prec != TT_FP64;
+  const double loc_eps = eps / std::sqrt((double)d);
+  orth_right(c, x, 0);
+  Iface PX, QX;
+  PX.init(c, d);
+  QX.init(c, d);
+  DBuf T1, T2, T3, W, Wt, W32, bm, rhs, sol, old;
+  auto right_all = [&]() {
+    for (int k = d - 1; k >= 2; --k) {
+      const int m = x.n[k];
+      right_update(c, PX.R[k + 1].p(), x.core[k].p(), Aop.a_jbai[k].p(), x.core[k].p(), x.r[k], A.r[k], x.r[k], m, m,
+                   A.r[k + 1], x.r[k + 1], x.r[k + 1], PX.R[k], T1, T2);
+      vright_update(c, QX.R[k + 1].p(), x.core[k].p(), b.core[k].p(), x.r[k], b.r[k], m, x.r[k + 1], b.r[k + 1],
+                    QX.R[k], T3);
+    }
+  };
+  right_all();
+  LocalSolver LS;
+  double maxdx = 0.0;
+  long long git = 0;
+  int swp = 0;
+  for (swp = 0; swp < nswp; ++swp) {
+    maxdx = 0.0;
+    for (int k = 0; k + 1 < d; ++k) {
+      const int n1 = x.n[k], n2 = x.n[k + 1], nn = n1 * n2;
+      const int r0 = x.r[k], r1 = x.r[k + 1], r2 = x.r[k + 2];
+      const int R0 = A.r[k], R1 = A.r[k + 1], R2 = A.r[k + 2];
+      // merged operator core in the local-matvec layout (R0, in, out, R2):
+      // W[a, (i1 i2), (o1 o2), c] = sum_b A_k[a, i1, o1, b] A_{k+1}[b, i2, o2, c]
+      Wt.ensure(c, (size_t)R0 * n1 * n1 * n2 * n2 * R2);
+      gemm(c, false, false, R0 * n1 * n1, n2 * n2 * R2, R1, 1.0, Aop.a_ajib[k].p(), R1, 0, Aop.a_ajib[k + 1].p(),
+           n2 * n2 * R2, 0, 0.0, Wt.p(), n2 * n2 * R2, 0);
+      W.ensure(c, (size_t)R0 * nn * nn * R2);
+      {
+        const int shape[6] = {R0, n1, n1, n2, n2, R2};
+        const int perm[6] = {0, 1, 3, 2, 4, 5};
+        permute(c, Wt.p(), W.p(), 6, shape, perm);
+      }
+      if (mixed) {
+        W32.ensure(c, ((size_t)R0 * nn * nn * R2 + 1) / 2);
+        d2f(c, W.p(), reinterpret_cast<float *>(W32.p()), (size_t)R0 * nn * nn * R2);
+      }
+      // merged right-hand side and initial guess
+      bm.ensure(c, (size_t)b.r[k] * nn * b.r[k + 2]);
+      gemm(c, false, false, b.r[k] * n1, n2 * b.r[k + 2], b.r[k + 1], 1.0, b.core[k].p(), b.r[k + 1], 0,
+           b.core[k + 1].p(), n2 * b.r[k + 2], 0, 0.0, bm.p(), n2 * b.r[k + 2], 0);
+      const size_t N = (size_t)r0 * nn * r2;
+      rhs.ensure(c, N);
+      vlocal(c, QX.L[k].p(), bm.p(), QX.R[k + 2].p(), r0, b.r[k], nn, b.r[k + 2], r2, rhs.p(), T3);
+      sol.ensure(c, N);
+      gemm(c, false, false, r0 * n1, n2 * r2, r1, 1.0, x.core[k].p(), r1, 0, x.core[k + 1].p(), n2 * r2, 0, 0.0,
+           sol.p(), n2 * r2, 0);
+      old.ensure(c, N);
+      copy(c, old.p(), sol.p(), N);
+      git += LS.solve(c, prec, PX.L[k].p(), W.p(), mixed ? reinterpret_cast<const float *>(W32.p()) : nullptr,
+                      PX.R[k + 2].p(), r0, R0, nn, R2, r2, rhs.p(), sol.p(), loc_eps);
+      axpby(c, N, 1.0, sol.p(), -1.0, old.p());
+      const double ns = nrm2(c, sol.p(), N);
+      const double dx = ns > 0 ? nrm2(c, old.p(), N) / ns : 0.0;
+      if (!std::isfinite(dx)) throw Error(TT_ENONFINITE, "dmrg_solve: non-finite local solution");
+      maxdx = std::max(maxdx, dx);
+      // split the supercore: X_k = U (left-orthogonal), X_{k+1} = S V^T
+      SVD sv;
+      svd_rm(c, sol.p(), r0 * n1, n2 * r2, sv, SVD_ORTH_U);
+      double sn2 = 0;
+      for (double v : sv.Sh) sn2 += v * v;
+      const int rk = trunc_rank(sv.Sh, loc_eps * std::sqrt(sn2), rmax);
+      DBuf xk(c, (size_t)r0 * n1 * rk), xk1(c, (size_t)rk * n2 * r2);
+      transpose(c, sv.Ut.p(), xk.p(), rk, r0 * n1);
+      copy(c, xk1.p(), sv.Vt.p(), (size_t)rk * n2 * r2);
+      scale_rows(c, xk1.p(), rk, n2 * r2, sv.S.p());
+      x.core[k] = std::move(xk);
+      x.core[k + 1] = std::move(xk1);
+      x.r[k + 1] = rk;
+      if (k + 2 < d) {
+        left_update(c, PX.L[k].p(), x.core[k].p(), Aop.a_ajib[k].p(), x.core[k].p(), r0, R0, r0, n1, n1, R1, rk, rk,
+                    PX.L[k + 1], T1, T2);
+        vleft_update(c, QX.L[k].p(), x.core[k].p(), b.core[k].p(), r0, b.r[k], n1, rk, b.r[k + 1], QX.L[k + 1], T3);
+      }
+    }
+    if (maxdx < eps) {
+      ++swp;
+      break;
+    }
+    if (swp + 1 < nswp) {
+      orth_right(c, x, 0);
+      right_all();
+    }
+  }
+  if (st) {
+    st->sweeps = std::min(swp, nswp);
+    st->max_dx = maxdx;
+    st->gmres_iters = git;
   }
 }
 

@@ -482,6 +482,22 @@ int tt_solve_local(tt_ctx *ctx, const tt_op *A, const tt_vec *b, tt_vec *x, doub
   return rc;
 }
 
+int tt_solve_dmrg(tt_ctx *ctx, const tt_op *A, const tt_vec *b, tt_vec *x, double eps, int rmax, int max_sweeps,
+                  tt_prec prec, int *sweeps_done, double *rel_change) {
+  return guarded(ctx, [&] {
+    TT_REQUIRE(A && b && x, "null argument");
+    TT_REQUIRE(eps > 0 && eps < 1 && max_sweeps >= 1, "tt_solve_dmrg: bad eps or max_sweeps");
+    TT_REQUIRE(prec == TT_FP64 || prec == TT_FP32_REFINED || prec == TT_TF32_SPLIT || prec == TT_BF16_SPLIT,
+               "tt_solve_dmrg: prec must be TT_FP64, TT_FP32_REFINED, TT_TF32_SPLIT or TT_BF16_SPLIT");
+    tt_op *Am = const_cast<tt_op *>(A);
+    tt::SolveStats st;
+    tt::dmrg_solve(&ctx->c, Am->op, b->t, x->t, eps, rmax, max_sweeps, &st, (int)prec);
+    if (sweeps_done) *sweeps_done = st.sweeps;
+    if (rel_change) *rel_change = st.max_dx;
+    if (st.max_dx >= eps) throw tt::Error(TT_ENOCONV, "tt_solve_dmrg: max_sweeps reached");
+  });
+}
+
 int tt_scalar_flux(tt_ctx *ctx, const tt_vec *psi, const double *w_host, int n_dir, tt_vec **phi) {
   return guarded(ctx, [&] {
     TT_REQUIRE(psi && w_host && phi, "null argument");
@@ -533,6 +549,7 @@ int keig_default_opts(keig_opts *o) {
   o->psi0_cores = nullptr;
   o->mv_kind = 0;
   o->local_form = 0;
+  o->solve_method = 0;
   return TT_OK;
 }
 
@@ -551,6 +568,9 @@ void check_opts(const keig_opts *opts) {
   TT_REQUIRE(opts->scheme == 0 || opts->scheme == 1, "keig: scheme must be 0 or 1");
   TT_REQUIRE(opts->mv_kind == 0 || opts->mv_kind == 1, "keig: mv_kind must be 0 or 1");
   TT_REQUIRE(opts->local_form == 0 || opts->local_form == 1, "keig: local_form must be 0 or 1");
+  TT_REQUIRE(opts->solve_method >= 0 && opts->solve_method <= 2, "keig: solve_method must be 0, 1 or 2");
+  TT_REQUIRE(!(opts->solve_method == 2 && opts->local_form == 1),
+             "keig: the two-site DMRG solve uses Galerkin local systems (local_form 0)");
 }
 
 // The operators of one problem, forward or transposed (adjoint).
@@ -656,15 +676,20 @@ bool run_fixed_point(tt::Ctx *c, KeigOps &ops, const keig_opts *opts, keig_resul
       tt::PhaseTimer pt(c, "keig.mv");
       tt::amen_mv(c, ops.RHS, psi, B, opts->eps, opts->rmax, opts->mv_sweeps, opts->kick, seed + 1000 + it, &mst);
     }
-    tt::TT psi_new = tt::tt_clone(c, psi);
+    // warm start from Psi; ALS, whose ranks never grow, starts from B (whose
+    // ranks the enriched product adapts)
+    tt::TT psi_new = tt::tt_clone(c, opts->solve_method == 1 ? B : psi);
     {
       tt::PhaseTimer pt(c, "keig.solve");
-      if (ops.ls)
-        tt::amen_solve(c, ops.N, B, psi_new, opts->eps, opts->rmax, opts->solve_sweeps, opts->kick,
-                       seed + 5000 + it, &sst, (int)opts->prec, &ops.MT);
+      const int kick = opts->solve_method == 1 ? 0 : opts->kick;  // ALS: no enrichment
+      if (opts->solve_method == 2)
+        tt::dmrg_solve(c, ops.LHS, B, psi_new, opts->eps, opts->rmax, opts->solve_sweeps, &sst, (int)opts->prec);
+      else if (ops.ls)
+        tt::amen_solve(c, ops.N, B, psi_new, opts->eps, opts->rmax, opts->solve_sweeps, kick, seed + 5000 + it,
+                       &sst, (int)opts->prec, &ops.MT);
       else
-        tt::amen_solve(c, ops.LHS, B, psi_new, opts->eps, opts->rmax, opts->solve_sweeps, opts->kick,
-                       seed + 5000 + it, &sst, (int)opts->prec);
+        tt::amen_solve(c, ops.LHS, B, psi_new, opts->eps, opts->rmax, opts->solve_sweeps, kick, seed + 5000 + it,
+                       &sst, (int)opts->prec);
     }
     if (c->phase_timing)
       fprintf(stderr, "keig it %d k %.12f mv_sweeps %d mv_dx %.2e solve_sweeps %d solve_dx %.2e gmres %lld ranks B %d psi %d\n",

@@ -98,6 +98,9 @@ struct SolveStats {
 // rhs_op = M^T gives the least-squares local systems of min ||M x - b||
 void amen_solve(Ctx *c, TTOp &A, const TT &b, TT &x, double eps, int rmax, int nswp, int kick,
                 uint64_t seed, SolveStats *st, int prec = TT_FP64, TTOp *rhs_op = nullptr);
+// two-site DMRG (merged pairs of cores, SVD split); Galerkin local systems
+void dmrg_solve(Ctx *c, TTOp &A, const TT &b, TT &x, double eps, int rmax, int nswp, SolveStats *st,
+                int prec = TT_FP64);
 void amen_mv(Ctx *c, TTOp &A, const TT &x, TT &y, double eps, int rmax, int nswp, int kick,
              uint64_t seed, SolveStats *st);
 // interface updates (amen.cu); operator cores in the permuted layouts of TTOp
