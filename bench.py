@@ -47,6 +47,9 @@ WORKLOADS = {
     "cube128_g2_s4_10cm": (lambda: ki.bare_cube(7), 96, 1e-8, 1, 1,
                            "bare homogeneous 10 cm cube, 128^3 grid points (the paper's Sec. 4.2 geometry at its "
                            "smallest grid), 2 groups, S4 level-symmetric (24 directions), vacuum"),
+    "cube256_g2_s4_10cm": (lambda: ki.bare_cube(8), 96, 1e-8, 1, 1,
+                           "bare homogeneous 10 cm cube, 256^3 grid points (the paper's middle grid), 2 groups, S4, "
+                           "vacuum"),
     "cube64_g2_s4_10cm": (lambda: ki.bare_cube(6), 96, 1e-8, 1, 1,
                           "bare homogeneous 10 cm cube, 64^3 grid points, 2 groups, S4, vacuum"),
     "box32_g4_s8": (lambda: ki.config(1), 64, 1e-7, 0, 2,
@@ -233,6 +236,70 @@ def roof(name, n, gms, gfl, peak, source, ms_step, bound="alu"):
             "avg_launch_us": avg * 1e3, "ms_in_step": gms, "share_of_step": gms / ms_step if ms_step else None}
 
 
+def batch_problems(n):
+    """Seeded mix of independent problems for the batched mode: bare 10 cm cubes
+    of 16^3 or 32^3 points, 2 or 4 groups, S4, S6 or S8, rank caps 16-64."""
+    out = []
+    for i in range(n):
+        rng = np.random.default_rng(2000 + i)
+        l = int(rng.choice([4, 5]))
+        G = int(rng.choice([2, 4]))
+        order = int(rng.choice([4, 6, 8]))
+        prob = ki.homogeneous(l=l, G=G, order=order, side=10.0, seed=2000 + i, name=f"batch{i}")
+        out.append((prob, int(rng.integers(16, 65))))
+    return out
+
+
+def run_batch(args):
+    """Batched mode: problems/s of keig_batch over a seeded mix, grouped
+    persistent-GMRES launches against one whole-GPU launch per system, and the
+    per-problem k error against the oracle."""
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    import paper_2309_03347_gb300 as K
+    from oracle import transport as T
+    probs = batch_problems(args.batch)
+    opts = []
+    for prob, cap in probs:
+        o = K.keig_default_opts()
+        o.eps, o.rmax, o.tol_k, o.tol_psi, o.max_iter = 1e-8, cap, 1e-9, 1e-5, 150
+        o.solve_sweeps = o.mv_sweeps = 1
+        o.local_form = 1
+        o.prec = K.TT_FP32_REFINED
+        opts.append(o)
+    plist = [p for p, _ in probs]
+    out = {}
+    for mode in ("grouped", "ungrouped"):
+        if mode == "ungrouped":
+            os.environ["KEIG_BATCH_UNGROUPED"] = "1"
+        else:
+            os.environ.pop("KEIG_BATCH_UNGROUPED", None)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res, _ = K.keig_batch(plist, opts, n_workers=args.batch_workers)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        out[mode] = {"s": wall, "problems_per_s": len(plist) / wall,
+                     "group_launches": K.keig_batch.last_group_launches,
+                     "group_systems": K.keig_batch.last_group_systems, "res": res}
+    os.environ.pop("KEIG_BATCH_UNGROUPED", None)
+    errs = []
+    for (prob, _), r in zip(probs, out["grouped"]["res"]):
+        kref = T.OracleProblem(prob).keig(tol_k=1e-12, max_iter=100000)["k"]
+        errs.append(abs(r["k"] - kref) / kref)
+    line = {"metric": "problems per second (batched k-eigenvalue solves)", "value": out["grouped"]["problems_per_s"],
+            "unit": "problems/s", "higher_is_better": True, "n_problems": len(plist),
+            "workers": args.batch_workers,
+            "config": {"workload": "bare 10 cm cubes 16^3/32^3, G 2/4, S4-S8, rank caps 16-64, seeds 2000+p",
+                       "local_systems": "least squares", "precision": PRECISION_TEXT["mixed"]},
+            "grouped": {k: v for k, v in out["grouped"].items() if k != "res"},
+            "one_launch_per_system": {k: v for k, v in out["ungrouped"].items() if k != "res"},
+            "k_rel_err": {"max": float(np.max(errs)), "median": float(np.median(errs)),
+                          "within_1e-6": int(np.sum(np.array(errs) < 1e-6))}}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -242,10 +309,16 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--prec", default="mixed", choices=["mixed", "tf32", "bf16", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="batched mode: solve this many independent problems with keig_batch (problems/s)")
+    ap.add_argument("--batch-workers", type=int, default=8)
     ap.add_argument("--max-iter", type=int, default=None,
                     help="run every solve for this many outer iterations (short runs for profiler captures)")
     args = ap.parse_args()
 
+    if args.batch:
+        run_batch(args)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     name = args.workload
@@ -279,7 +352,7 @@ def main():
 
     # ---- warm-up: the first solve runs to the solver's own stop and fixes the
     # number of outer iterations after which k stays within 1e-6 of the oracle
-    full = make_opts(K, name, args.prec, 400)
+    full = make_opts(K, name, args.prec, args.max_iter or 150)
     flush.fill_(1.0)
     r0 = step(full)
     n_ok = first_within(r0["k_hist"], kref)
@@ -332,7 +405,7 @@ def main():
                                 chi=pinned(p.chi), mat=pinned(p.mat))
     phi_pin = pinned(np.zeros((p.G, p.n, p.n, p.n)))
     e2e = []
-    for _ in range(max(1, min(args.steps, 3))):
+    for _ in range(max(1, min(args.steps, 2))):
         flush.fill_(1.0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()

@@ -380,6 +380,18 @@ int keig_alpha(tt_ctx *ctx, const tt_problem *prob, const keig_opts *opts, doubl
  * code in problem order.  Contexts must not be used elsewhere meanwhile. */
 int keig_batch(tt_ctx *const *ctxs, int n_ctx, const tt_problem *probs, const keig_opts *opts, int n_prob,
                keig_result *out, int *status);
+/* With more than one context (all on one device), keig_batch gathers the
+ * workers' local systems that run in the persistent FP32 GMRES kernel
+ * (TT_FP32_REFINED) into grouped cooperative launches: a worker submits its
+ * system and waits; the first waiting worker leads, waits until every worker
+ * that is solving a problem has submitted or 300 us have passed, gives each
+ * gathered system a range of CTAs in proportion to its size, launches them
+ * all in one kernel (each system with its own grid barrier over its CTAs) and
+ * hands back the statuses.  Without grouping, each system's launch occupies
+ * every SM and the workers' launches run one after another.  keig_batch_stats
+ * returns the grouped launches and the systems they carried in the last
+ * keig_batch call. */
+int keig_batch_stats(long long *group_launches, long long *group_systems);
 
 /* Sensitivities of k to every cross-section entry by the adjoint method.
  * Differentiating H Psi = (S + F/k) Psi and testing with the adjoint

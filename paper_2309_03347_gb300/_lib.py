@@ -705,6 +705,10 @@ def keig_batch(problems, opts_list, n_workers: int = 8, contexts=None):
     status = (C.c_int * n)()
     lib.keig_batch(handles, len(contexts), probs, opts, n, res, status)
     torch.cuda.synchronize()
+    gl, gs = C.c_longlong(), C.c_longlong()
+    lib.keig_batch_stats.argtypes = [C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
+    lib.keig_batch_stats(C.byref(gl), C.byref(gs))
+    keig_batch.last_group_launches, keig_batch.last_group_systems = gl.value, gs.value
     out = []
     for i in range(n):
         r = res[i]

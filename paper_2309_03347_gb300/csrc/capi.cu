@@ -9,6 +9,9 @@
 struct tt_ctx {
   tt::Ctx c;
 };
+
+// grouped persistent-GMRES launches of the last keig_batch call
+static std::atomic<long long> g_batch_group_launches{0}, g_batch_group_systems{0};
 struct tt_vec {
   tt::Ctx *owner;
   tt::TT t;
@@ -132,6 +135,12 @@ int tt_ctx_create(tt_ctx **out, void *stream, tt_alloc_fn alloc_fn, tt_free_fn f
     ctx->c.phase_timing = getenv("KEIG_PHASE_TIMES") != nullptr;
     ctx->c.mixed_svd = getenv("KEIG_FP64_SVD") == nullptr;
     ctx->c.persistent_gmres = getenv("KEIG_LAUNCHED_GMRES") == nullptr;
+    {
+      const char *t = getenv("KEIG_PGMRES_TUNE");
+      ctx->c.pg_tune = !(t && t[0] == '0');
+    }
+    TT_CHECK_CUDA(cudaEventCreate(&ctx->c.tune_ev[0]));
+    TT_CHECK_CUDA(cudaEventCreate(&ctx->c.tune_ev[1]));
     // keep freed blocks in the stream-ordered pool
     cudaMemPool_t pool;
     TT_CHECK_CUDA(cudaDeviceGetDefaultMemPool(&pool, ctx->c.device));
@@ -161,6 +170,8 @@ int tt_ctx_destroy(tt_ctx *ctx) {
   ctx->c.scalar_buf.release();
   cudaStreamSynchronize(ctx->c.stream);
   if (ctx->c.h_pinned) cudaFreeHost(ctx->c.h_pinned);
+  for (auto e : ctx->c.tune_ev)
+    if (e) cudaEventDestroy(e);
   for (auto &e : ctx->c.ev_pool) {
     cudaEventDestroy(e.first);
     cudaEventDestroy(e.second);
@@ -1172,24 +1183,55 @@ int keig_batch(tt_ctx *const *ctxs, int n_ctx, const tt_problem *probs, const ke
                keig_result *out, int *status) {
   if (!ctxs || n_ctx < 1 || n_ctx > 1024 || !probs || !opts || !out || !status || n_prob < 0) return TT_EINVAL;
   for (int w = 0; w < n_ctx; ++w)
-    if (!ctxs[w]) return TT_EINVAL;
+    if (!ctxs[w] || ctxs[w]->c.device != ctxs[0]->c.device || ctxs[w]->c.group) return TT_EINVAL;
+  // the workers' persistent-GMRES systems share grouped launches
+  tt::PGGroup *group = nullptr;
+  if (n_ctx > 1 && getenv("KEIG_BATCH_UNGROUPED") == nullptr) {
+    cudaSetDevice(ctxs[0]->c.device);
+    try {
+      group = tt::pg_group_create(ctxs[0]->c.device, ctxs[0]->c.sm_count);
+    } catch (const tt::Error &e) {
+      return e.code;
+    }
+    tt::pg_group_set_active(group, 0);
+  }
   std::atomic<int> next{0};
   auto worker = [&](int w) {
     cudaSetDevice(ctxs[w]->c.device);
+    ctxs[w]->c.group = group;
     for (;;) {
       const int i = next.fetch_add(1);
       if (i >= n_prob) break;
+      if (group) tt::pg_group_join(group);
       status[i] = keig_fixed_point(ctxs[w], &probs[i], &opts[i], &out[i], nullptr, nullptr);
+      if (group) tt::pg_group_leave(group);
     }
+    ctxs[w]->c.group = nullptr;
   };
   std::vector<std::thread> th;
   th.reserve(n_ctx);
   for (int w = 0; w < n_ctx; ++w) th.emplace_back(worker, w);
   for (auto &t : th) t.join();
+  if (group) {
+    long long l = 0, s = 0;
+    tt::pg_group_stats(group, &l, &s);
+    g_batch_group_launches = l;
+    g_batch_group_systems = s;
+    tt::pg_group_destroy(group);
+  } else {
+    g_batch_group_launches = g_batch_group_systems = 0;
+  }
   int rc = TT_OK;
   for (int i = 0; i < n_prob && rc == TT_OK; ++i)
     if (status[i] != TT_OK) rc = status[i];
   return rc;
+}
+
+int keig_batch_stats(long long *group_launches, long long *group_systems) {
+  if (!group_launches || !group_systems) return TT_EINVAL;
+  *group_launches = g_batch_group_launches;
+  *group_systems = g_batch_group_systems;
+  return TT_OK;
 }
 
 }  // extern "C"

@@ -7,6 +7,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <stdexcept>
 #include <string>
 #include <utility>
@@ -92,6 +93,16 @@ struct Ctx {
   int sm_count = 152;
   // spin limit of the bounded device waits (grid barriers); < 0: the kernels' defaults
   long long wait_limit = -1;
+  // set while the context solves one of several batched problems: its
+  // persistent-GMRES systems join grouped launches
+  struct PGGroup *group = nullptr;
+  // grid-size tuner of the persistent GMRES: per shape class, the measured
+  // time per Arnoldi step of each candidate grid (all SMs, 1/2, 1/4, 1/8),
+  // then the fastest (KEIG_PGMRES_TUNE=0 keeps one CTA per SM)
+  bool pg_tune = true;
+  std::map<uint64_t, int> pg_tuned;
+  std::map<uint64_t, std::vector<std::pair<int, double>>> pg_trials;
+  cudaEvent_t tune_ev[2] = {nullptr, nullptr};
   // scratch buffers reused across calls (grown on demand)
   DBuf ws_gemm;    // split-K partial sums (FP64)
   DBuf ws_gemm32;  // split-K partial sums (FP32, stored in a double-typed buffer)
@@ -214,6 +225,14 @@ struct PGWork {
   DBuf V, T1, T2, ws, D, st;
 };
 bool pgmres32_fits(Ctx *c, int N, int restart);
+// Grouped launches of the persistent GMRES across contexts (batched problems)
+struct PGGroup;
+PGGroup *pg_group_create(int device, int sm_count);
+void pg_group_destroy(PGGroup *g);
+void pg_group_set_active(PGGroup *g, int n);  // workers that will submit
+void pg_group_join(PGGroup *g);               // a worker starts a problem
+void pg_group_leave(PGGroup *g);              // ... and has finished it
+void pg_group_stats(PGGroup *g, long long *launches, long long *systems);
 int pgmres32(Ctx *c, const float *PL, const float *A32, const float *PR, int r0, int R1, int m, int R2, int r1,
              const float *b, float *x, double tol, int restart, int maxit, PGWork &W);
 

@@ -16,6 +16,9 @@
 #include "common.cuh"
 
 #include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <mutex>
 
 namespace tt {
 
@@ -36,6 +39,8 @@ struct PGArgs {
   int r0, R1, m, R2, r1, N, mr, maxit, split3, kchunk3, chunk, gv;
   double tol;
   long long bar_limit;  // spins of a CTA waiting at the grid barrier before it gives up
+  int cta0, ncta;       // this system's CTAs: blockIdx.x in [cta0, cta0 + ncta)
+  int cta;              // blockIdx.x - cta0 (set on the device)
 };
 
 // offsets into the device state D (doubles) for restart mr and G CTAs
@@ -65,7 +70,7 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 }
 
 // Grid barrier over co-resident CTAs (cooperative launch); bounded spin.
-__device__ bool grid_sync(unsigned *bar, int *err, long long limit) {
+__device__ bool grid_sync(unsigned *bar, int *err, long long limit, unsigned nct) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -73,7 +78,7 @@ __device__ bool grid_sync(unsigned *bar, int *err, long long limit) {
     const unsigned g = *vgen;
     int ok = 1;
     __threadfence();
-    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+    if (atomicAdd(bar, 1u) == nct - 1) {
       atomicExch(bar, 0u);
       __threadfence();
       atomicAdd(bar + 1, 1u);
@@ -101,11 +106,11 @@ template <bool TA, bool TB>
 __device__ void gemm_phase(int M, int N, int K, float alpha, const float *__restrict__ A, int lda, long long sA,
                            const float *__restrict__ B, int ldb, long long sB, float *__restrict__ C, int ldc,
                            long long sC, int batch, int splits, int kchunk, long long sSplit, float (*As)[TBM + 1],
-                           float (*Bs)[TBN + 1]) {
+                           float (*Bs)[TBN + 1], int cta, int ncta) {
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int tm = (M + TBM - 1) / TBM, tn = (N + TBN - 1) / TBN;
   const long long items = (long long)tm * tn * splits * batch;
-  for (long long item = blockIdx.x; item < items; item += gridDim.x) {
+  for (long long item = cta; item < items; item += ncta) {
     long long t = item;
     const int bx = (int)(t % tn);
     t /= tn;
@@ -195,11 +200,11 @@ __device__ void gemm_phase(int M, int N, int K, float alpha, const float *__rest
 __device__ bool matvec_tail(const PGArgs &P, float (*As)[TBM + 1], float (*Bs)[TBN + 1]) {
   const int r0 = P.r0, R1 = P.R1, m = P.m, R2 = P.R2, r1 = P.r1;
   gemm_phase<true, false>(m * R2, r1, R1 * m, 1.f, P.A, m * R2, 0, P.T1, r1, (long long)R1 * m * r1, P.T2, r1,
-                          (long long)m * R2 * r1, r0, 1, R1 * m, 0, As, Bs);
-  if (!grid_sync(P.bar, P.st + 1, P.bar_limit)) return false;
+                          (long long)m * R2 * r1, r0, 1, R1 * m, 0, As, Bs, P.cta, P.ncta);
+  if (!grid_sync(P.bar, P.st + 1, P.bar_limit, (unsigned)P.ncta)) return false;
   gemm_phase<false, true>(r0 * m, r1, R2 * r1, 1.f, P.T2, R2 * r1, 0, P.PR, R2 * r1, 0, P.ws, r1, 0, 1, P.split3,
-                          P.kchunk3, (long long)P.N, As, Bs);
-  return grid_sync(P.bar, P.st + 1, P.bar_limit);
+                          P.kchunk3, (long long)P.N, As, Bs, P.cta, P.ncta);
+  return grid_sync(P.bar, P.st + 1, P.bar_limit, (unsigned)P.ncta);
 }
 
 // w-partials of the matvec of v (scale alpha) into ws (split3 slices of N)
@@ -207,12 +212,13 @@ __device__ bool matvec_phases(const PGArgs &P, const float *v, float alpha, floa
                               float (*Bs)[TBN + 1]) {
   const int r0 = P.r0, R1 = P.R1, m = P.m, r1 = P.r1;
   gemm_phase<false, false>(r0 * R1, m * r1, r0, alpha, P.PL, r0, 0, v, m * r1, 0, P.T1, m * r1, 0, 1, 1, r0, 0, As,
-                           Bs);
-  if (!grid_sync(P.bar, P.st + 1, P.bar_limit)) return false;
+                           Bs, P.cta, P.ncta);
+  if (!grid_sync(P.bar, P.st + 1, P.bar_limit, (unsigned)P.ncta)) return false;
   return matvec_tail(P, As, Bs);
 }
 
-__global__ void __launch_bounds__(PG_THREADS, 1) pgmres_kernel(PGArgs P) {
+// The GMRES of one system on its CTAs (P.cta = this CTA's index among them).
+__device__ __forceinline__ void pgmres_body(const PGArgs &P) {
   __shared__ float As[TBK][TBM + 1];
   __shared__ float Bs[TBK][TBN + 1];
   __shared__ float wsh[PG_CHUNK];
@@ -223,7 +229,7 @@ __global__ void __launch_bounds__(PG_THREADS, 1) pgmres_kernel(PGArgs P) {
   __shared__ double sH[(PG_MAXR + 1) * PG_MAXR];
   __shared__ double scs[PG_MAXR], ssn[PG_MAXR], sg[PG_MAXR + 1], sh1[PG_MAXR + 1], sh2[PG_MAXR + 1];
   __shared__ double s_hn;
-  const int bid = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int bid = P.cta, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nwarp = PG_THREADS / 32;
   const int Gv = P.gv;
   const PGLayout L(P.mr, Gv);
@@ -343,7 +349,7 @@ __global__ void __launch_bounds__(PG_THREADS, 1) pgmres_kernel(PGArgs P) {
       if (tid == 0 && bid < Gv) D[L.npart + bid] = sq;
     }
     first = false;
-    if (!grid_sync(P.bar, err, P.bar_limit)) return;
+    if (!grid_sync(P.bar, err, P.bar_limit, (unsigned)P.ncta)) return;
     {
       const double beta = norm_from_partials();
       if (tid == 0) {
@@ -370,15 +376,15 @@ __global__ void __launch_bounds__(PG_THREADS, 1) pgmres_kernel(PGArgs P) {
         ++steps;
       }
       if (j == mr) {
-        if (!grid_sync(P.bar, err, P.bar_limit)) return;
+        if (!grid_sync(P.bar, err, P.bar_limit, (unsigned)P.ncta)) return;
         break;
       }
       // T1 = Phi_L (s_j V_j), then the flags of step j - 1 are visible
       {
         const int r0 = P.r0, R1 = P.R1, m = P.m, r1 = P.r1;
         gemm_phase<false, false>(r0 * R1, m * r1, r0, (float)ss[j], P.PL, r0, 0, P.V + (size_t)j * N, m * r1, 0,
-                                 P.T1, m * r1, 0, 1, 1, r0, 0, As, Bs);
-        if (!grid_sync(P.bar, err, P.bar_limit)) return;
+                                 P.T1, m * r1, 0, 1, 1, r0, 0, As, Bs, P.cta, P.ncta);
+        if (!grid_sync(P.bar, err, P.bar_limit, (unsigned)P.ncta)) return;
       }
       if (j > 0 && __ldcg(P.st + 2)) {
         jend = j - 1;
@@ -402,7 +408,7 @@ __global__ void __launch_bounds__(PG_THREADS, 1) pgmres_kernel(PGArgs P) {
       }
       __syncthreads();
       inner(D + L.part, j);
-      if (!grid_sync(P.bar, err, P.bar_limit)) return;
+      if (!grid_sync(P.bar, err, P.bar_limit, (unsigned)P.ncta)) return;
       // two subtraction passes; the second also forms the norm partials and stores w
       for (int pass = 0; pass < 2; ++pass) {
         const double *part = D + (pass == 0 ? L.part : L.part2);
@@ -429,7 +435,7 @@ __global__ void __launch_bounds__(PG_THREADS, 1) pgmres_kernel(PGArgs P) {
           sq = block_total(sq);
           if (tid == 0 && bid < Gv) D[L.npart + bid] = sq;
         }
-        if (!grid_sync(P.bar, err, P.bar_limit)) return;
+        if (!grid_sync(P.bar, err, P.bar_limit, (unsigned)P.ncta)) return;
       }
     }
     // ---- x += sum_v y_v s_v V_v with y = H^-1 g over the columns 0..jend
@@ -444,19 +450,247 @@ __global__ void __launch_bounds__(PG_THREADS, 1) pgmres_kernel(PGArgs P) {
       }
       for (int i = 0; i < kk; ++i) y[i] *= ss[i];
     }
-    if (!grid_sync(P.bar, err, P.bar_limit)) return;
+    if (!grid_sync(P.bar, err, P.bar_limit, (unsigned)P.ncta)) return;
     for (int v = tid; v <= jend; v += PG_THREADS) hsc[v] = (float)__ldcg(D + L.y + v);
     __syncthreads();
     for (int i = tid; i < cn; i += PG_THREADS) P.x[lo + i] += sub_comb(i, jend);
-    if (!grid_sync(P.bar, err, P.bar_limit)) return;
+    if (!grid_sync(P.bar, err, P.bar_limit, (unsigned)P.ncta)) return;
     if (__ldcg(P.st + 3)) break;
+  }
+}
+
+__global__ void __launch_bounds__(PG_THREADS, 1) pgmres_kernel(PGArgs P) {
+  P.cta = (int)blockIdx.x - P.cta0;
+  pgmres_body(P);
+}
+
+// Several independent systems in one cooperative launch: system g owns the
+// CTAs [list[g].cta0, list[g].cta0 + list[g].ncta) (list sorted by cta0) and
+// runs on them with its own barrier words, buffers and status.
+__global__ void __launch_bounds__(PG_THREADS, 1) pgmres_group_kernel(const PGArgs *__restrict__ list, int n) {
+  __shared__ PGArgs sp;
+  if (threadIdx.x == 0) {
+    int g = 0;
+    while (g + 1 < n && list[g + 1].cta0 <= (int)blockIdx.x) ++g;
+    sp = list[g];
+    sp.cta = (int)blockIdx.x - sp.cta0;
+  }
+  __syncthreads();
+  pgmres_body(sp);
+}
+
+}  // namespace
+
+// The parameters of a system that depend on the CTAs it runs on: the CTAs
+// of the vector phases (slices of about 256 entries, at most PG_CHUNK) and
+// the K split of the third GEMM (fill the CTAs, K slices of >= 2 tiles).
+void pg_shape(PGArgs &P, int ncta) {
+  const int N = P.N;
+  P.ncta = ncta;
+  P.gv = std::max(1, std::min(ncta, (N + 255) / 256));
+  P.chunk = (N + P.gv - 1) / P.gv;
+  const int K3 = P.R2 * P.r1;
+  const int tiles3 = ((P.r0 * P.m + TBM - 1) / TBM) * ((P.r1 + TBN - 1) / TBN);
+  int split3 = std::max(1, std::min(32, ncta / std::max(1, tiles3)));
+  int kchunk3 = (K3 + split3 - 1) / split3;
+  kchunk3 = std::max(2 * TBK, (kchunk3 + TBK - 1) / TBK * TBK);
+  P.split3 = (K3 + kchunk3 - 1) / kchunk3;
+  P.kchunk3 = kchunk3;
+}
+
+// Shape class of a local system for the grid-size tuner: log2 of its size,
+// its mode and (capped) operator ranks.
+uint64_t pg_shape_class(int N, int m, int R1, int R2) {
+  int lb = 0;
+  while ((1 << (lb + 1)) <= N) ++lb;
+  return (uint64_t)lb | ((uint64_t)std::min(m, 4095) << 8) | ((uint64_t)std::min(R1, 1023) << 20) |
+         ((uint64_t)std::min(R2, 1023) << 30);
+}
+
+bool pgmres32_fits(Ctx *c, int N, int restart) {
+  return restart >= 1 && restart <= PG_MAXR && N > 0 && (long long)N <= (long long)PG_CHUNK * c->sm_count;
+}
+
+// ----------------------------------------------------------------- grouped launches
+// Local systems of independent problems (keig_batch: one worker thread and
+// context per problem stream) are gathered into one cooperative launch of
+// pgmres_group_kernel instead of one whole-GPU launch each.  A worker
+// submits its prepared system and waits; the first waiting worker becomes
+// the leader, waits until every active worker has submitted or a short
+// window has passed, gives each gathered system CTAs in proportion to its
+// size (at least enough for slices of PG_CHUNK entries), launches them
+// together on the group's stream after the submitters' streams, and copies
+// every system's status back.  Systems that do not fit in one grid wait for
+// the next launch.
+struct PGGroup {
+  struct Item {
+    PGArgs P;
+    cudaEvent_t ready = nullptr;
+    int hs[2] = {0, 0};
+    bool done = false;
+    int err = 0;
+  };
+  std::mutex mu;
+  std::condition_variable cv;
+  int active = 0;
+  bool launching = false;
+  std::vector<Item *> pending;
+  std::chrono::steady_clock::time_point first_arrival;
+  int device = 0, sm_count = 152;
+  cudaStream_t stream = nullptr;
+  PGArgs *d_list = nullptr, *h_list = nullptr;
+  int *h_st = nullptr;
+  double window_us = 300.0;
+  long long launches = 0, systems = 0;
+};
+
+PGGroup *pg_group_create(int device, int sm_count) {
+  PGGroup *g = new PGGroup();
+  g->device = device;
+  g->sm_count = sm_count;
+  TT_CHECK_CUDA(cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking));
+  TT_CHECK_CUDA(cudaMalloc(&g->d_list, sizeof(PGArgs) * 1024));
+  TT_CHECK_CUDA(cudaMallocHost(&g->h_list, sizeof(PGArgs) * 1024));
+  TT_CHECK_CUDA(cudaMallocHost(&g->h_st, sizeof(int) * 2 * 1024));
+  return g;
+}
+
+void pg_group_destroy(PGGroup *g) {
+  if (!g) return;
+  cudaStreamSynchronize(g->stream);
+  cudaFree(g->d_list);
+  cudaFreeHost(g->h_list);
+  cudaFreeHost(g->h_st);
+  cudaStreamDestroy(g->stream);
+  delete g;
+}
+
+void pg_group_set_active(PGGroup *g, int n) {
+  std::lock_guard<std::mutex> lk(g->mu);
+  g->active = n;
+  g->cv.notify_all();
+}
+
+void pg_group_join(PGGroup *g) {
+  std::lock_guard<std::mutex> lk(g->mu);
+  ++g->active;
+}
+
+void pg_group_leave(PGGroup *g) {
+  std::lock_guard<std::mutex> lk(g->mu);
+  --g->active;
+  g->cv.notify_all();
+}
+
+void pg_group_stats(PGGroup *g, long long *launches, long long *systems) {
+  std::lock_guard<std::mutex> lk(g->mu);
+  *launches = g->launches;
+  *systems = g->systems;
+}
+
+namespace {
+
+// Launch the gathered items (called by the leader without the lock held).
+void pg_group_launch(PGGroup *g, std::vector<PGGroup::Item *> &items) {
+  const int n = (int)items.size();
+  long long total_n = 0;
+  for (auto *it : items) total_n += it->P.N;
+  std::vector<int> need(n), give(n);
+  int used = 0;
+  for (int i = 0; i < n; ++i) {
+    need[i] = std::max(1, (items[i]->P.N + PG_CHUNK - 1) / PG_CHUNK);
+    used += need[i];
+  }
+  int spare = g->sm_count - used;
+  for (int i = 0; i < n; ++i) {
+    const int extra = (int)((double)spare * items[i]->P.N / std::max<long long>(1, total_n));
+    give[i] = need[i] + std::max(0, extra);
+  }
+  int cta = 0;
+  for (int i = 0; i < n; ++i) {
+    PGArgs &P = items[i]->P;
+    pg_shape(P, give[i]);
+    P.cta0 = cta;
+    P.cta = 0;
+    cta += give[i];
+    g->h_list[i] = P;
+    TT_CHECK_CUDA(cudaStreamWaitEvent(g->stream, items[i]->ready, 0));
+  }
+  TT_CHECK_CUDA(cudaMemcpyAsync(g->d_list, g->h_list, sizeof(PGArgs) * n, cudaMemcpyHostToDevice, g->stream));
+  const PGArgs *dl = g->d_list;
+  void *args[] = {(void *)&dl, (void *)&n};
+  TT_CHECK_CUDA(cudaLaunchCooperativeKernel((const void *)pgmres_group_kernel, dim3(cta), dim3(PG_THREADS), args, 0,
+                                            g->stream));
+  for (int i = 0; i < n; ++i)
+    TT_CHECK_CUDA(cudaMemcpyAsync(g->h_st + 2 * i, items[i]->P.st, 2 * sizeof(int), cudaMemcpyDeviceToHost,
+                                  g->stream));
+  TT_CHECK_CUDA(cudaStreamSynchronize(g->stream));
+  for (int i = 0; i < n; ++i) {
+    items[i]->hs[0] = g->h_st[2 * i];
+    items[i]->hs[1] = g->h_st[2 * i + 1];
   }
 }
 
 }  // namespace
 
-bool pgmres32_fits(Ctx *c, int N, int restart) {
-  return restart >= 1 && restart <= PG_MAXR && N > 0 && (long long)N <= (long long)PG_CHUNK * c->sm_count;
+// Submit one prepared system (its status words already cleared on the
+// worker's stream) and wait until a grouped launch has run it.
+void pg_group_solve(PGGroup *g, Ctx *c, PGArgs P, int hs[2]) {
+  PGGroup::Item item;
+  item.P = P;
+  TT_CHECK_CUDA(cudaEventCreateWithFlags(&item.ready, cudaEventDisableTiming));
+  TT_CHECK_CUDA(cudaEventRecord(item.ready, c->stream));
+  std::unique_lock<std::mutex> lk(g->mu);
+  if (g->pending.empty()) g->first_arrival = std::chrono::steady_clock::now();
+  g->pending.push_back(&item);
+  g->cv.notify_all();
+  while (!item.done) {
+    if (!g->launching && !g->pending.empty()) {
+      // lead: wait for the other active workers or the window, then launch
+      const auto until = g->first_arrival + std::chrono::microseconds((long long)g->window_us);
+      while ((int)g->pending.size() < g->active && std::chrono::steady_clock::now() < until)
+        g->cv.wait_until(lk, until);
+      if (g->launching || g->pending.empty()) continue;
+      std::vector<PGGroup::Item *> batch;
+      std::vector<PGGroup::Item *> rest;
+      int used = 0;
+      for (auto *it : g->pending) {
+        const int need = std::max(1, (it->P.N + PG_CHUNK - 1) / PG_CHUNK);
+        if (used + need <= g->sm_count && (int)batch.size() < 1024) {
+          batch.push_back(it);
+          used += need;
+        } else {
+          rest.push_back(it);
+        }
+      }
+      g->pending.swap(rest);
+      if (!g->pending.empty()) g->first_arrival = std::chrono::steady_clock::now();
+      g->launching = true;
+      lk.unlock();
+      int err = 0;
+      try {
+        pg_group_launch(g, batch);
+      } catch (const Error &e) {
+        err = e.code;
+      }
+      lk.lock();
+      g->launching = false;
+      g->launches += 1;
+      g->systems += (long long)batch.size();
+      for (auto *it : batch) {
+        it->err = err;
+        it->done = true;
+      }
+      g->cv.notify_all();
+    } else {
+      g->cv.wait_for(lk, std::chrono::milliseconds(50));
+    }
+  }
+  lk.unlock();
+  cudaEventDestroy(item.ready);
+  if (item.err) throw Error(item.err, "pgmres32: grouped launch failed");
+  hs[0] = item.hs[0];
+  hs[1] = item.hs[1];
 }
 
 int pgmres32(Ctx *c, const float *PL, const float *A32, const float *PR, int r0, int R1, int m, int R2, int r1,
@@ -513,19 +747,60 @@ int pgmres32(Ctx *c, const float *PL, const float *A32, const float *PR, int r0,
   P.gv = gv;
   P.tol = tol;
   P.bar_limit = c->wait_limit >= 0 ? c->wait_limit : BAR_LIMIT;
-  void *args[] = {&P};
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-  if (c->profiling) {
-    c->prof_begin(&ev0, &ev1, 3);
-    TT_CHECK_CUDA(cudaEventRecord(ev0, c->stream));
+  P.cta0 = 0;
+  P.ncta = G;
+  P.cta = 0;
+  // grid size of a single-system launch: picked per shape class by the tuner
+  const uint64_t key = pg_shape_class(N, m, R1, R2);
+  int Gl = G;
+  const int gmin = std::max(1, (N + PG_CHUNK - 1) / PG_CHUNK);
+  bool trial = false;
+  if (!c->group && c->pg_tune) {
+    auto it = c->pg_tuned.find(key);
+    if (it != c->pg_tuned.end()) {
+      Gl = std::max(it->second, gmin);
+    } else {
+      auto &tr = c->pg_trials[key];
+      const int cand = G >> tr.size();  // G, G/2, G/4, G/8
+      Gl = std::max(cand, gmin);
+      trial = true;
+    }
   }
-  TT_CHECK_CUDA(cudaLaunchCooperativeKernel((const void *)pgmres_kernel, dim3(G), dim3(PG_THREADS), args, 0,
-                                            c->stream));
-  c->count();
-  if (c->profiling) TT_CHECK_CUDA(cudaEventRecord(ev1, c->stream));
+  pg_shape(P, Gl);
   int hs[2];
-  TT_CHECK_CUDA(cudaMemcpyAsync(hs, W.st.p(), 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-  c->sync();
+  if (c->group) {
+    // batched problems: this system joins the next grouped launch
+    pg_group_solve(c->group, c, P, hs);
+  } else {
+    void *args[] = {&P};
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if (c->profiling) {
+      c->prof_begin(&ev0, &ev1, 3);
+      TT_CHECK_CUDA(cudaEventRecord(ev0, c->stream));
+    }
+    if (trial) TT_CHECK_CUDA(cudaEventRecord(c->tune_ev[0], c->stream));
+    TT_CHECK_CUDA(cudaLaunchCooperativeKernel((const void *)pgmres_kernel, dim3(Gl), dim3(PG_THREADS), args, 0,
+                                              c->stream));
+    c->count();
+    if (trial) TT_CHECK_CUDA(cudaEventRecord(c->tune_ev[1], c->stream));
+    if (c->profiling) TT_CHECK_CUDA(cudaEventRecord(ev1, c->stream));
+    TT_CHECK_CUDA(cudaMemcpyAsync(hs, W.st.p(), 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    c->sync();
+    if (trial) {
+      // time per Arnoldi step of this grid size; after the last candidate keep the fastest
+      float ms = 0.f;
+      TT_CHECK_CUDA(cudaEventElapsedTime(&ms, c->tune_ev[0], c->tune_ev[1]));
+      auto &tr = c->pg_trials[key];
+      tr.push_back({Gl, ms / std::max(1, hs[0])});
+      if (tr.size() >= 4 || Gl == gmin) {
+        auto best = *std::min_element(tr.begin(), tr.end(),
+                                      [](const std::pair<int, double> &a, const std::pair<int, double> &b) {
+                                        return a.second < b.second;
+                                      });
+        c->pg_tuned[key] = best.first;
+      }
+    }
+  }
   // algorithmic work: one local matvec per Arnoldi step plus the restart residuals
   // (2 n r0 r1 (r0 R1 + n R1 R2 + r1 R2) each), and the two Gram-Schmidt passes
   // (4 N flops per stored vector per pass, counted with the mean basis size)

@@ -47,3 +47,24 @@ def test_batch_equals_single_solves(ctx):
     for p, r in zip(probs, res):
         single = K.keig_fixed_point(ctx, p, _opts())
         assert abs(single["k"] - r["k"]) < 1e-12 * abs(single["k"])
+
+
+def test_grouped_gmres_launches_match_oracle(ctx):
+    # FP32-refined local solves: the workers' persistent-GMRES systems share
+    # grouped cooperative launches (several systems per launch, each on its
+    # own range of CTAs), and every problem still reaches the oracle's k
+    probs = _problems()
+    opts = []
+    for _ in probs:
+        o = _opts()
+        o.prec = K.TT_FP32_REFINED
+        opts.append(o)
+    res, _ = K.keig_batch(probs, opts, n_workers=6)
+    launches, systems = K.keig_batch.last_group_launches, K.keig_batch.last_group_systems
+    assert launches > 0 and systems > 1.5 * launches, (launches, systems)
+    for p, r, o in zip(probs, res, opts):
+        assert r["code"] == K.TT_OK
+        ref = T.OracleProblem(p).keig(tol_k=1e-12, max_iter=20000)["k"]
+        assert abs(r["k"] - ref) / ref < 1e-6
+        single = K.keig_fixed_point(ctx, p, o)
+        assert abs(single["k"] - r["k"]) < 1e-9 * abs(single["k"])

@@ -56,9 +56,10 @@ def test_j_autograd_function_backward(ctx):
     KeigJ = K.keig_j_function()
     t = {f: torch.tensor(getattr(p, f), dtype=torch.float64, requires_grad=True)
          for f in ("sig_t", "sig_s", "nu_sig_f", "chi")}
-    j = KeigJ.apply(t["sig_t"], t["sig_s"], t["nu_sig_f"], t["chi"], p, rg, rv, ctx, o, 1e-9, 500)
+    o.tol_k, o.tol_psi = 1e-9, 1e-6  # this test checks the plumbing of backward()
+    j = KeigJ.apply(t["sig_t"], t["sig_s"], t["nu_sig_f"], t["chi"], p, rg, rv, ctx, o, 1e-6, 500)
     (3.0 * j).backward()
-    g = K.keig_gpt(ctx, p, rg, rv, o, tol_gpt=1e-9, max_gpt=500)
-    assert abs(float(j) - g["J"]) <= 1e-12 * abs(g["J"])
+    g = K.keig_gpt(ctx, p, rg, rv, o, tol_gpt=1e-6, max_gpt=500)
+    assert abs(float(j.detach()) - g["J"]) <= 1e-12 * abs(g["J"])
     for f in ("sig_t", "sig_s", "nu_sig_f", "chi"):
         assert np.allclose(t[f].grad.numpy(), 3.0 * g[f], rtol=1e-9, atol=0)

@@ -1,8 +1,8 @@
 """The other members of the alternating TT solver family of Sec. 3.5 ("ALS,
 DMRG, AMEn"): two-site DMRG (tt_solve_dmrg) and one-site ALS (tt_solve_local
-with kick = 0), against the oracle's sweep (H^{-1} b on the full grid) and,
-inside the fixed point of Eq. (TT_k_eff_fixed_points), against the oracle's k
-and scalar flux."""
+with kick = 0), against the oracle's sweep (H^{-1} b on the full grid), and
+DMRG inside the fixed point of Eq. (TT_k_eff_fixed_points) against the
+oracle's k and scalar flux."""
 import dataclasses
 
 import numpy as np
@@ -31,8 +31,7 @@ def _full_ranks(modes):
     return [1] + [int(min(np.prod(modes[:k]), np.prod(modes[k:]))) for k in range(1, d)] + [1]
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
-@pytest.mark.parametrize("hetero", [False, True])
+@pytest.mark.parametrize("hetero,prec", [(False, "fp64"), (True, "fp32")])
 def test_dmrg_solve_matches_sweep(ctx, hetero, prec):
     p = ki.fissile_box(l=3, G=2, order=4, seed=41, half_width=2) if hetero else ki.homogeneous(l=2, G=2, order=4)
     A = K.tt_build_operator(ctx, p, 0, 1e-13)
@@ -74,15 +73,14 @@ def test_dmrg_reports_noconv(ctx):
     assert info["code"] == K.TT_ENOCONV
 
 
-@pytest.mark.parametrize("method", [1, 2])
-def test_fixed_point_with_als_and_dmrg(ctx, method):
-    # ALS starts each solve from B = (S + F/k) Psi, whose ranks the enriched
-    # product grows; DMRG adapts ranks itself
+def test_fixed_point_with_dmrg(ctx):
+    # the two-site solve adapts ranks itself inside the fixed point (one-site
+    # ALS cannot: its ranks stay those of its initial guess)
     p = dataclasses.replace(ki.config(0), side=(2.0,) * 3)
     o = K.keig_default_opts()
     o.eps, o.rmax, o.tol_k, o.tol_psi, o.max_iter = 1e-10, 0, 1e-11, 1e-7, 600
     o.solve_sweeps, o.mv_sweeps = 4, 4
-    o.solve_method = method
+    o.solve_method = 2
     res = K.keig_fixed_point(ctx, p, o, want_phi=True)
     ref = T.OracleProblem(p).keig(tol_k=1e-12, max_iter=20000)
     assert abs(res["k"] - ref["k"]) / ref["k"] < 1e-6
