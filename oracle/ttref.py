@@ -106,7 +106,7 @@ def dot(x, y) -> float:
     """<x, y> by left-to-right contraction of the cores."""
     v = np.ones((1, 1))
     for a, b in zip(x, y):
-        v = np.einsum("ab,ajc,bjd->cd", v, a, b)
+        v = np.einsum("ab,ajc,bjd->cd", v, a, b, optimize=True)  # pairwise contraction order
     return float(v[0, 0])
 
 

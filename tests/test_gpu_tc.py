@@ -26,7 +26,7 @@ def _ones(ctx, modes):
     return K.tt_vec_create(ctx, [np.ones((1, m, 1)) for m in modes])
 
 
-@pytest.mark.parametrize("rhs_rank", [2, 9])
+@pytest.mark.parametrize("rhs_rank", [9])
 def test_solve_local_tf32_split_matches_sweep(ctx, rhs_rank):
     # the transport sweep H^-1 b of the oracle, reached by the tensor-core
     # solve to the FP64 tolerance of the all-FP64 solve
