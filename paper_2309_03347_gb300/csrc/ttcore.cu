@@ -430,7 +430,13 @@ void to_dense(Ctx *c, const TT &x, double *dst, size_t len) {
   for (int k = 1; k < x.d; ++k) {
     const int rk = x.r[k], cols = x.n[k] * x.r[k + 1];
     b.ensure(c, rows * cols);
-    gemm(c, false, false, (int)rows, cols, rk, 1.0, a.p(), rk, 0, x.core[k].p(), cols, 0, 0.0, b.p(), cols, 0);
+    // row blocks keep every GEMM launch inside its grid limit
+    const size_t blk = (size_t)1 << 21;
+    for (size_t r0 = 0; r0 < rows; r0 += blk) {
+      const int mr = (int)std::min(blk, rows - r0);
+      gemm(c, false, false, mr, cols, rk, 1.0, a.p() + r0 * rk, rk, 0, x.core[k].p(), cols, 0, 0.0,
+           b.p() + r0 * cols, cols, 0);
+    }
     a.swap(b);
     rows *= x.n[k];
   }
