@@ -317,9 +317,10 @@ typedef struct {
                           be singular; N's projections are symmetric positive definite.
                         Applies to keig_fixed_point (other entry points use 0). */
   int solve_method;  /* the alternating method of the linear solve (Sec. 3.5, "ALS, DMRG, AMEn"):
-                        0 AMEn (one site, residual enrichment of rank kick); 1 ALS (one site, no
-                        enrichment: ranks never grow above those of the initial guess);
-                        2 two-site DMRG (tt_solve_dmrg; Galerkin local systems only) */
+                        0 AMEn (one site, residual enrichment of rank kick); 2 two-site DMRG
+                        (tt_solve_dmrg; Galerkin local systems only).  One-site ALS (tt_solve_local
+                        with kick = 0) keeps the ranks of its initial guess, so it is not offered
+                        inside the fixed point (TT_EINVAL for 1) */
 } keig_opts;
 
 typedef struct {

@@ -579,7 +579,9 @@ void check_opts(const keig_opts *opts) {
   TT_REQUIRE(opts->scheme == 0 || opts->scheme == 1, "keig: scheme must be 0 or 1");
   TT_REQUIRE(opts->mv_kind == 0 || opts->mv_kind == 1, "keig: mv_kind must be 0 or 1");
   TT_REQUIRE(opts->local_form == 0 || opts->local_form == 1, "keig: local_form must be 0 or 1");
-  TT_REQUIRE(opts->solve_method >= 0 && opts->solve_method <= 2, "keig: solve_method must be 0, 1 or 2");
+  TT_REQUIRE(opts->solve_method == 0 || opts->solve_method == 2,
+             "keig: solve_method must be 0 (AMEn) or 2 (two-site DMRG); one-site ALS (tt_solve_local with "
+             "kick 0) keeps the ranks of its initial guess and does not converge inside the fixed point");
   TT_REQUIRE(!(opts->solve_method == 2 && opts->local_form == 1),
              "keig: the two-site DMRG solve uses Galerkin local systems (local_form 0)");
 }
@@ -687,12 +689,10 @@ bool run_fixed_point(tt::Ctx *c, KeigOps &ops, const keig_opts *opts, keig_resul
       tt::PhaseTimer pt(c, "keig.mv");
       tt::amen_mv(c, ops.RHS, psi, B, opts->eps, opts->rmax, opts->mv_sweeps, opts->kick, seed + 1000 + it, &mst);
     }
-    // warm start from Psi; ALS, whose ranks never grow, starts from B (whose
-    // ranks the enriched product adapts)
-    tt::TT psi_new = tt::tt_clone(c, opts->solve_method == 1 ? B : psi);
+    tt::TT psi_new = tt::tt_clone(c, psi);
     {
       tt::PhaseTimer pt(c, "keig.solve");
-      const int kick = opts->solve_method == 1 ? 0 : opts->kick;  // ALS: no enrichment
+      const int kick = opts->kick;
       if (opts->solve_method == 2)
         tt::dmrg_solve(c, ops.LHS, B, psi_new, opts->eps, opts->rmax, opts->solve_sweeps, &sst, (int)opts->prec);
       else if (ops.ls)
