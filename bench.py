@@ -82,7 +82,14 @@ def golden_reference(name):
 
 
 def cpu_model():
-    """The host CPU's model name (from /proc/cpuinfo; 'unknown' if absent)."""
+    """The host CPU's model name (lscpu, else /proc/cpuinfo; 'unknown' if absent)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
     try:
         for line in open("/proc/cpuinfo"):
             key = line.split(":")[0].strip().lower()
